@@ -295,6 +295,29 @@ void orc_adjoint_M_rows(const double *G, const uint64_t *hp, int d, int log2b,
         }
 }
 
+/* One entry of the sketch straight from its definition (the bucketed product
+ * that Compress reaches, Sec. 3.2 with Algorithm 1):
+ *   R_r[w] = sum_{(i,j) : h1_r(i) XOR h2_r(j) = w} s1_r(i) s2_r(j) C[i][j],
+ * C[i][j] = sum_t A[i][t] B[t][j], visiting every (i, j).  For sampled checks
+ * of large problems where Compress itself would take too long on the CPU. */
+double orc_R_entry(const double *A, int64_t lda, int transA, const double *B, int64_t ldb,
+                   int64_t m, int64_t k, int64_t p, int log2b, const uint64_t *hp_r,
+                   uint32_t w)
+{
+    double acc = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        uint32_t hi = orc_bucket(hp_r[0], hp_r[1], (uint64_t)i, log2b);
+        int si = orc_sign(hp_r[4], hp_r[5], (uint64_t)i);
+        for (int64_t j = 0; j < p; ++j) {
+            if ((hi ^ orc_bucket(hp_r[2], hp_r[3], (uint64_t)j, log2b)) != w) continue;
+            double c = 0.0;
+            for (int64_t t = 0; t < k; ++t) c += orc_A(A, lda, transA, i, t) * B[t * ldb + j];
+            acc += (double)(si * orc_sign(hp_r[6], hp_r[7], (uint64_t)j)) * c;
+        }
+    }
+    return acc;
+}
+
 int orc_openmp_max_threads(void)
 {
 #ifdef _OPENMP

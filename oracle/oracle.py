@@ -72,6 +72,8 @@ def _load():
         lib.orc_mean_at_pairs.argtypes = [P, P, i32, i32, i64, P, P, P]
         lib.orc_adjoint_G.argtypes = [P, i32, i32, i64, P, P, P, P]
         lib.orc_adjoint_M_rows.argtypes = [P, P, i32, i32, i64, i64, i64, P, i64]
+        lib.orc_R_entry.argtypes = [P, i64, i32, P, i64, i64, i64, i64, i32, P, ctypes.c_uint32]
+        lib.orc_R_entry.restype = f64
         lib.orc_openmp_max_threads.restype = i32
         _lib = lib
         return lib
@@ -153,6 +155,20 @@ def compress(A, B, hp: np.ndarray, log2b: int, transA: bool = False,
     if rc != 0:
         raise MemoryError("oracle compress failed")
     return R
+
+
+def R_entry(A, B, hp: np.ndarray, log2b: int, r: int, w: int, transA: bool = False) -> float:
+    """R_r[w] from the bucket definition (every (i, j) visited; O(m p) + O(k) per pair)."""
+    A = _f64(A)
+    B = _f64(B)
+    if transA:
+        k, m = A.shape
+    else:
+        m, k = A.shape
+    p = B.shape[1]
+    hr = np.ascontiguousarray(hp[r], dtype=np.uint64)
+    return float(_load().orc_R_entry(_ptr(A), A.shape[1], int(transA), _ptr(B), B.shape[1],
+                                     m, k, p, log2b, _ptr(hr), w))
 
 
 def decompress(R: np.ndarray, hp: np.ndarray, i: int, j: int, reduce: int = MEDIAN) -> float:

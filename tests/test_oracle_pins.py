@@ -358,3 +358,15 @@ def test_adjoint_equals_dense_jacobian():
             jac[i, t] = _loss(E, B, hp, L, I, J, W) - base
     np.testing.assert_allclose(dA, jac, rtol=0, atol=1e-12)
     assert dB.shape == B.shape
+
+
+def test_R_entry_matches_compress():
+    g = np.random.default_rng(41)
+    A = g.standard_normal((40, 13))
+    B = g.standard_normal((13, 35))
+    hp = orc.draw_hashes(77, 2)
+    R = orc.compress(A, B, hp, 6)
+    for r, w in [(0, 0), (1, 17), (0, 63), (1, 5)]:
+        assert abs(orc.R_entry(A, B, hp, 6, r, w) - R[r, w]) < 1e-12 * 40
+    At = np.ascontiguousarray(A.T)
+    assert abs(orc.R_entry(At, B, hp, 6, 1, 9, transA=True) - R[1, 9]) < 1e-12 * 40
