@@ -1,0 +1,164 @@
+/*
+ * cmm.h -- C ABI of libcmm, compressed matrix multiplication in the Fast
+ * Walsh-Hadamard Transform form on one GB300 GPU (sm_103a).
+ *
+ * Method (Andersson & Karppa, "Engineering Compressed Matrix Multiplication
+ * with the Fast Walsh-Hadamard Transform", arXiv 2601.09477, Algorithm 1):
+ * for every repetition r < d, column t of A and row t of B are hashed into
+ * signed sketches of length b = 2^log2b,
+ *     x_t[u] = sum_{i : h1(i) = u} s1(i) A[i][t],   y_t[u] = sum_{j : h2(j) = u} s2(j) B[t][j],
+ * transformed with the unnormalised Walsh-Hadamard matrix H[u][v] = (-1)^popcount(u & v),
+ * multiplied pointwise and summed over t, then transformed back and scaled:
+ *     R_r = (1/b) H sum_t (H x_t) o (H y_t)      (so R_r = sum_t x_t XOR-convolved with y_t).
+ * The estimate of C = A B is Chat[i][j] = median_r s1_r(i) s2_r(j) R_r[h1_r(i) XOR h2_r(j)]
+ * (Algorithm 1, Decompress).  The hashes are the multiply-add-shift family of
+ * Sec. 4.2: h_{a,c}(x) = ((a x + c) mod 2^64) >> (64 - log2 b); a sign hash is
+ * the same family with b = 2, +1 when that top bit is 0 and -1 when it is 1.
+ *
+ * Conventions for every entry point:
+ *  - Matrices are row-major.  A is m x k (lda >= k) or, with transA = 1, the
+ *    array holds A^T as k x m (lda >= m), the layout of Sec. 4.3.  B is k x p
+ *    (ldb >= p).  Row/column indices are 0-based and are the hash keys, so
+ *    m, p < 2^31.
+ *  - Pointers named "device" are CUDA device (or managed) memory owned by the
+ *    caller; the library never allocates or frees device memory.  Scratch space
+ *    is the caller's `ws` buffer of at least the size the matching
+ *    *_workspace_bytes query returns, 256-byte aligned.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls are asynchronous on that stream unless stated otherwise.
+ *  - Argument errors are returned before anything is launched.  Every call
+ *    returns a cmm_status; cmm_last_error() gives a message for the calling
+ *    host thread.
+ */
+#ifndef CMM_H
+#define CMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CMM_MAX_D 64        /* largest number of repetitions d */
+#define CMM_MAX_LOG2B 24    /* largest sketch length b = 2^24 */
+
+typedef enum {
+    CMM_OK = 0,
+    CMM_ERR_ARG = -1,        /* null pointer, negative size, bad enum, bad leading dimension */
+    CMM_ERR_RANGE = -3,      /* size outside the supported range (d, log2b, m, p, k) */
+    CMM_ERR_CAPACITY = -4,   /* heavy-hitter list longer than `capacity`; *count is the true size */
+    CMM_ERR_CUDA = -5,       /* a CUDA runtime call or launch failed */
+    CMM_ERR_TIMEOUT = -6,    /* a bounded device-side wait ran out (batched launch) */
+    CMM_ERR_WORKSPACE = -8   /* ws is NULL, misaligned or smaller than the query returned */
+} cmm_status;
+
+/* storage type of A and B */
+typedef enum { CMM_F64 = 0, CMM_F32 = 1, CMM_BF16 = 2 } cmm_dtype;
+
+/* arithmetic of the sketch transforms and the per-block multiply-accumulate.
+ * The cross-block reduction of R over t, the inverse transform and the
+ * extraction are FP64 in every precision. */
+typedef enum {
+    CMM_PREC_F64 = 0,     /* FP64 butterflies and accumulation ("plain FP64") */
+    CMM_PREC_F32 = 1,     /* FP32 butterflies, FP32 accumulation within a block of t */
+    CMM_PREC_BF16TC = 2   /* BF16 operands with exact +-1 Hadamard blocks on the tensor cores, FP32 accumulation */
+} cmm_prec;
+
+/* how the d repetitions are combined */
+typedef enum { CMM_MEDIAN = 0, CMM_MEAN = 1 } cmm_reduce;
+
+/* Hash functions of all repetitions (Sec. 4.2).  `params` is a HOST array of
+ * 8*d words; for repetition r the words 8r .. 8r+7 are
+ *   a, c of h1 (rows of A -> buckets),  a, c of h2 (columns of B -> buckets),
+ *   a, c of s1 (row signs),             a, c of s2 (column signs).
+ * The library copies them into kernel parameters; the array may be freed after
+ * the call returns. */
+typedef struct {
+    int32_t d;               /* repetitions, 1 .. CMM_MAX_D */
+    int32_t log2b;           /* sketch length b = 2^log2b, 1 .. CMM_MAX_LOG2B */
+    const uint64_t *params;  /* host, 8*d words */
+} cmm_hashes;
+
+/* Fill `params` (host, 8*d words) from a 64-bit seed with splitmix64
+ * (Steele, Lea & Flood 2014): the words are its successive outputs in the
+ * order of cmm_hashes.params.  The paper draws (a, c) as "two random 64-bit
+ * integers" (Sec. 4.2) and fixes no generator; this one is the library's
+ * convention.  Errors: CMM_ERR_ARG (params NULL), CMM_ERR_RANGE (d). */
+int cmm_make_hashes(uint64_t seed, int32_t d, uint64_t *params);
+
+/* Bytes of `ws` needed by cmm_sketch for these sizes (0 on invalid sizes). */
+size_t cmm_sketch_workspace_bytes(int64_t m, int64_t k, int64_t p, int32_t d, int32_t log2b,
+                                  int32_t dtype, int32_t prec, int32_t transA);
+
+/* Compress (Algorithm 1): R (device, d x b FP64, row-major) = the sketch of
+ * A B for every repetition, already scaled by 1/b, i.e.
+ *   R_r[w] = sum_{(i,j) : h1_r(i) XOR h2_r(j) = w} s1_r(i) s2_r(j) (A B)[i][j]
+ * up to the rounding of the chosen precision.  A, B: device, `dtype`.
+ * k = 0 gives R = 0.  Errors: CMM_ERR_ARG, CMM_ERR_RANGE, CMM_ERR_WORKSPACE,
+ * CMM_ERR_CUDA. */
+int cmm_sketch(const void *A, int64_t lda, int32_t transA, const void *B, int64_t ldb,
+               int32_t dtype, int64_t m, int64_t k, int64_t p, const cmm_hashes *hs,
+               int32_t prec, double *R, void *ws, size_t ws_bytes, void *stream);
+
+/* Bytes of `ws` needed by cmm_extract / cmm_heavy_hitters / cmm_threshold. */
+size_t cmm_extract_workspace_bytes(int64_t m, int64_t p, int32_t d);
+
+/* Decompress (Algorithm 1) for every entry: C (device, m x p FP64, ldc >= p)
+ *   C[i][j] = reduce_r s1_r(i) s2_r(j) R_r[h1_r(i) XOR h2_r(j)]
+ * with reduce = median (middle order statistic for odd d, mean of the two
+ * middle values for even d) or mean.  R: device, d x b FP64 from cmm_sketch.
+ * Errors: CMM_ERR_ARG, CMM_ERR_RANGE, CMM_ERR_WORKSPACE, CMM_ERR_CUDA. */
+int cmm_extract(const double *R, const cmm_hashes *hs, int64_t m, int64_t p, int32_t reduce,
+                double *C, int64_t ldc, void *ws, size_t ws_bytes, void *stream);
+
+/* Heavy hitters straight from the sketch (the goal of the method, Sec. 1):
+ * every (i, j) with |Chat[i][j]| >= tau, sorted by (i, j) row-major, written to
+ * I, J (device int32) and V (device FP64, the estimate) up to `capacity`
+ * entries.  *count (HOST) receives the total number found.  Synchronises
+ * `stream` to read the count.  Returns CMM_ERR_CAPACITY when *count >
+ * capacity (the first `capacity` entries are still written). */
+int cmm_heavy_hitters(const double *R, const cmm_hashes *hs, int64_t m, int64_t p,
+                      int32_t reduce, double tau, int32_t *I, int32_t *J, double *V,
+                      int64_t capacity, int64_t *count, void *ws, size_t ws_bytes,
+                      void *stream);
+
+/* The same list from a dense estimate C (device, m x p FP64, ldc): entries
+ * with |C[i][j]| >= tau in (i, j) order.  Same outputs and errors as
+ * cmm_heavy_hitters. */
+int cmm_threshold(const double *C, int64_t m, int64_t p, int64_t ldc, double tau,
+                  int32_t *I, int32_t *J, double *V, int64_t capacity, int64_t *count,
+                  void *ws, size_t ws_bytes, void *stream);
+
+/* Bytes of `ws` needed by cmm_multiply. */
+size_t cmm_multiply_workspace_bytes(int64_t m, int64_t k, int64_t p, int32_t d, int32_t log2b,
+                                    int32_t dtype, int32_t prec, int32_t transA);
+
+/* Compress then Decompress every entry: C (device, m x p FP64) = the estimate
+ * of A B.  R (device, d x b FP64) receives the sketch; it may be NULL, in
+ * which case the sketch lives in `ws`.  Errors: as cmm_sketch and cmm_extract. */
+int cmm_multiply(const void *A, int64_t lda, int32_t transA, const void *B, int64_t ldb,
+                 int32_t dtype, int64_t m, int64_t k, int64_t p, const cmm_hashes *hs,
+                 int32_t prec, int32_t reduce, double *C, int64_t ldc, double *R,
+                 void *ws, size_t ws_bytes, void *stream);
+
+/* Mean estimator at a list of P pairs (the differentiable form):
+ * out[q] = (1/d) sum_r s1_r(I[q]) s2_r(J[q]) R_r[h1_r(I[q]) XOR h2_r(J[q])].
+ * I, J: device int32 (0 <= I < m, 0 <= J < p, not checked on the device);
+ * out: device FP64.  The paper has no mean form; it is the unbiased
+ * single-repetition estimator of Sec. 3.1 averaged over r.
+ * Errors: CMM_ERR_ARG, CMM_ERR_RANGE, CMM_ERR_CUDA. */
+int cmm_mean_pairs(const double *R, const cmm_hashes *hs, int64_t P, const int32_t *I,
+                   const int32_t *J, double *out, void *stream);
+
+/* Last error message of the calling host thread ("" when none). */
+const char *cmm_last_error(void);
+
+/* Library version string. */
+const char *cmm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CMM_H */

@@ -1,0 +1,253 @@
+"""Python binding of libcmm (``include/cmm.h``): argument marshalling only.
+
+Every step of the path runs in the library's CUDA kernels; this module passes
+torch tensors' device pointers, sizes and the current CUDA stream through
+ctypes.  There is no CPU fallback: if ``libcmm.so`` is missing the import of
+this module fails.
+
+Method: Pagh's compressed matrix multiplication in the Fast Walsh-Hadamard
+Transform form (Andersson & Karppa, arXiv 2601.09477, Algorithm 1 and Sec. 4.2).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcmm.so")
+
+OK = 0
+ERR_ARG = -1
+ERR_RANGE = -3
+ERR_CAPACITY = -4
+ERR_CUDA = -5
+ERR_TIMEOUT = -6
+ERR_WORKSPACE = -8
+
+F64, F32, BF16 = 0, 1, 2
+PREC_F64, PREC_F32, PREC_BF16TC = 0, 1, 2
+MEDIAN, MEAN = 0, 1
+MAX_D = 64
+MAX_LOG2B = 24
+
+_PREC = {"f64": PREC_F64, "f32": PREC_F32, "bf16tc": PREC_BF16TC}
+_REDUCE = {"median": MEDIAN, "mean": MEAN}
+_DTYPE = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
+
+
+class CmmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("cmm error %d: %s" % (code, msg))
+        self.code = code
+
+
+class _Hashes(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("log2b", ctypes.c_int32),
+                ("params", ctypes.POINTER(ctypes.c_uint64))]
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libcmm.so is not built (expected at %s); run "
+                          "paper_2601_09477_gb300.build.build() first" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    i64, i32, u64, f64, sz = (ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
+                              ctypes.c_double, ctypes.c_size_t)
+    H = ctypes.POINTER(_Hashes)
+    sig = {
+        "cmm_make_hashes": (ctypes.c_int, [u64, i32, P]),
+        "cmm_sketch_workspace_bytes": (sz, [i64, i64, i64, i32, i32, i32, i32, i32]),
+        "cmm_sketch": (ctypes.c_int, [P, i64, i32, P, i64, i32, i64, i64, i64, H, i32, P, P, sz, P]),
+        "cmm_extract_workspace_bytes": (sz, [i64, i64, i32]),
+        "cmm_extract": (ctypes.c_int, [P, H, i64, i64, i32, P, i64, P, sz, P]),
+        "cmm_heavy_hitters": (ctypes.c_int, [P, H, i64, i64, i32, f64, P, P, P, i64,
+                                             ctypes.POINTER(ctypes.c_int64), P, sz, P]),
+        "cmm_threshold": (ctypes.c_int, [P, i64, i64, i64, f64, P, P, P, i64,
+                                         ctypes.POINTER(ctypes.c_int64), P, sz, P]),
+        "cmm_multiply_workspace_bytes": (sz, [i64, i64, i64, i32, i32, i32, i32, i32]),
+        "cmm_multiply": (ctypes.c_int, [P, i64, i32, P, i64, i32, i64, i64, i64, H, i32, i32,
+                                        P, i64, P, P, sz, P]),
+        "cmm_mean_pairs": (ctypes.c_int, [P, H, i64, P, P, P, P]),
+        "cmm_last_error": (ctypes.c_char_p, []),
+        "cmm_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def version() -> str:
+    return lib.cmm_version().decode()
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise CmmError(rc, lib.cmm_last_error().decode())
+
+
+@dataclass
+class Hashes:
+    """Hash functions of all repetitions: ``params`` is (d, 8) uint64 with, per
+    repetition, (a, c) of h1, h2, s1, s2 (Sec. 4.2)."""
+    d: int
+    log2b: int
+    params: np.ndarray
+
+    def __post_init__(self):
+        self.params = np.ascontiguousarray(self.params, dtype=np.uint64).reshape(self.d, 8)
+        self._c = _Hashes(self.d, self.log2b,
+                          self.params.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+
+    @property
+    def ref(self):
+        return ctypes.byref(self._c)
+
+    @property
+    def b(self) -> int:
+        return 1 << self.log2b
+
+
+def make_hashes(seed: int, d: int, log2b: int) -> Hashes:
+    params = np.zeros((d, 8), dtype=np.uint64)
+    _check(lib.cmm_make_hashes(seed & (2**64 - 1), d, params.ctypes.data))
+    return Hashes(d, log2b, params)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def _operands(A: torch.Tensor, B: torch.Tensor, transA: bool):
+    if A.dtype not in _DTYPE or B.dtype != A.dtype:
+        raise TypeError("A and B must share a dtype among float64, float32, bfloat16")
+    if A.dim() != 2 or B.dim() != 2:
+        raise ValueError("A and B must be matrices")
+    if A.stride(1) != 1 or B.stride(1) != 1:
+        raise ValueError("A and B must be row-major (unit stride along rows)")
+    if transA:
+        k, m = A.shape
+    else:
+        m, k = A.shape
+    k2, p = B.shape
+    if k != k2:
+        raise ValueError("inner dimensions differ: %d vs %d" % (k, k2))
+    return m, k, p, _DTYPE[A.dtype]
+
+
+def sketch(A: torch.Tensor, B: torch.Tensor, h: Hashes, prec: str = "f32",
+           transA: bool = False, stream=None) -> torch.Tensor:
+    """Compress (Algorithm 1): R (d x b, float64, device), scaled by 1/b."""
+    m, k, p, dt = _operands(A, B, transA)
+    pr = _PREC[prec]
+    ws = _workspace(lib.cmm_sketch_workspace_bytes(m, k, p, h.d, h.log2b, dt, pr, int(transA)),
+                    A.device)
+    R = torch.empty((h.d, h.b), dtype=torch.float64, device=A.device)
+    _check(lib.cmm_sketch(A.data_ptr(), max(A.stride(0), 1), int(transA), B.data_ptr(),
+                          max(B.stride(0), 1), dt, m, k, p, h.ref, pr, R.data_ptr(),
+                          ws.data_ptr(), ws.numel(), _stream(stream)))
+    return R
+
+
+def extract(R: torch.Tensor, h: Hashes, m: int, p: int, reduce: str = "median",
+            stream=None, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Decompress (Algorithm 1) every entry: the m x p float64 estimate."""
+    _check_R(R, h)
+    C = out if out is not None else torch.empty((m, p), dtype=torch.float64, device=R.device)
+    ws = _workspace(lib.cmm_extract_workspace_bytes(m, p, h.d), R.device)
+    _check(lib.cmm_extract(R.data_ptr(), h.ref, m, p, _REDUCE[reduce], C.data_ptr(),
+                           max(C.stride(0), 1), ws.data_ptr(), ws.numel(), _stream(stream)))
+    return C
+
+
+def _check_R(R: torch.Tensor, h: Hashes):
+    if R.dtype != torch.float64 or tuple(R.shape) != (h.d, h.b) or not R.is_contiguous():
+        raise ValueError("R must be a contiguous float64 (d, b) tensor")
+
+
+def heavy_hitters(R: torch.Tensor, h: Hashes, m: int, p: int, tau: float,
+                  reduce: str = "median", capacity: int = 1 << 20, stream=None):
+    """(I, J, V) of every |estimate| >= tau in (i, j) order, computed from R."""
+    _check_R(R, h)
+    dev = R.device
+    I = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+    J = torch.empty_like(I)
+    V = torch.empty(max(capacity, 1), dtype=torch.float64, device=dev)
+    cnt = ctypes.c_int64(0)
+    ws = _workspace(lib.cmm_extract_workspace_bytes(m, p, h.d), dev)
+    _check(lib.cmm_heavy_hitters(R.data_ptr(), h.ref, m, p, _REDUCE[reduce], float(tau),
+                                 I.data_ptr(), J.data_ptr(), V.data_ptr(), capacity,
+                                 ctypes.byref(cnt), ws.data_ptr(), ws.numel(), _stream(stream)))
+    n = cnt.value
+    return I[:n], J[:n], V[:n]
+
+
+def threshold(C: torch.Tensor, tau: float, capacity: int = 1 << 20, stream=None):
+    """(I, J, V) of every |C[i, j]| >= tau in (i, j) order, from a dense estimate."""
+    if C.dtype != torch.float64 or C.dim() != 2 or C.stride(1) != 1:
+        raise ValueError("C must be a row-major float64 matrix")
+    m, p = C.shape
+    dev = C.device
+    I = torch.empty(max(capacity, 1), dtype=torch.int32, device=dev)
+    J = torch.empty_like(I)
+    V = torch.empty(max(capacity, 1), dtype=torch.float64, device=dev)
+    cnt = ctypes.c_int64(0)
+    ws = _workspace(lib.cmm_extract_workspace_bytes(m, p, 1), dev)
+    _check(lib.cmm_threshold(C.data_ptr(), m, p, max(C.stride(0), 1), float(tau), I.data_ptr(),
+                             J.data_ptr(), V.data_ptr(), capacity, ctypes.byref(cnt),
+                             ws.data_ptr(), ws.numel(), _stream(stream)))
+    n = cnt.value
+    return I[:n], J[:n], V[:n]
+
+
+def multiply_workspace_bytes(m, k, p, h: Hashes, dtype, prec: str = "f32", transA=False) -> int:
+    return int(lib.cmm_multiply_workspace_bytes(m, k, p, h.d, h.log2b, _DTYPE[dtype],
+                                                _PREC[prec], int(transA)))
+
+
+def multiply(A: torch.Tensor, B: torch.Tensor, h: Hashes, prec: str = "f32",
+             reduce: str = "median", transA: bool = False, R: torch.Tensor | None = None,
+             out: torch.Tensor | None = None, ws: torch.Tensor | None = None, stream=None):
+    """Compress then Decompress every entry: the m x p float64 estimate of A B.
+    ``R`` (d x b float64) receives the sketch when given."""
+    m, k, p, dt = _operands(A, B, transA)
+    pr = _PREC[prec]
+    need = lib.cmm_multiply_workspace_bytes(m, k, p, h.d, h.log2b, dt, pr, int(transA))
+    if ws is None or ws.numel() < need:
+        ws = _workspace(need, A.device)
+    C = out if out is not None else torch.empty((m, p), dtype=torch.float64, device=A.device)
+    if R is not None:
+        _check_R(R, h)
+    _check(lib.cmm_multiply(A.data_ptr(), max(A.stride(0), 1), int(transA), B.data_ptr(),
+                            max(B.stride(0), 1), dt, m, k, p, h.ref, pr, _REDUCE[reduce],
+                            C.data_ptr(), max(C.stride(0), 1),
+                            R.data_ptr() if R is not None else None, ws.data_ptr(),
+                            ws.numel(), _stream(stream)))
+    return C
+
+
+def mean_pairs(R: torch.Tensor, h: Hashes, I: torch.Tensor, J: torch.Tensor,
+               stream=None) -> torch.Tensor:
+    """Mean-over-d estimator at pairs (I[q], J[q])."""
+    _check_R(R, h)
+    I = I.to(device=R.device, dtype=torch.int32).contiguous()
+    J = J.to(device=R.device, dtype=torch.int32).contiguous()
+    out = torch.empty(I.numel(), dtype=torch.float64, device=R.device)
+    _check(lib.cmm_mean_pairs(R.data_ptr(), h.ref, I.numel(), I.data_ptr(), J.data_ptr(),
+                              out.data_ptr(), _stream(stream)))
+    return out

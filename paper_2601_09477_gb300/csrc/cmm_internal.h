@@ -1,0 +1,83 @@
+// cmm_internal.h -- declarations shared by the library's host code and its
+// CUDA translation units (never by anything outside libcmm).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/cmm.h"
+
+namespace cmm {
+
+// Hash parameters of one repetition, passed by value in kernel parameters.
+struct HashRep {
+    uint64_t a1, c1;    // h1: rows of A -> buckets
+    uint64_t a2, c2;    // h2: columns of B -> buckets
+    uint64_t as1, cs1;  // s1: row signs
+    uint64_t as2, cs2;  // s2: column signs
+};
+
+struct HashParams {
+    HashRep rep[CMM_MAX_D];
+};
+
+// Largest transform slice one CTA holds, per butterfly precision.
+constexpr int kMaxLloF32 = 14;   // 2^14 FP32 = 64 KiB of shared memory
+constexpr int kMaxLloF64 = 13;   // 2^13 FP64 = 64 KiB
+constexpr int kFinishLlo = 12;   // FP64 slice of the inverse transform: 2^12 doubles = 32 KiB
+
+// Plan of one cmm_sketch call.
+struct SketchPlan {
+    int prec;              // CMM_PREC_*
+    int L;                 // log2 b
+    int Llo;               // log2 of the slice a CTA transforms
+    int C;                 // 2^(L - Llo) slices per repetition
+    int nchunks;           // blocks of the inner index
+    int64_t chunk;         // inner indices per block (last may be shorter)
+    int threads;           // CTA size
+    size_t smem;           // dynamic shared memory per CTA
+    // workspace carve-up (byte offsets into ws)
+    size_t off_At, off_Bp, off_partial, off_Z, total;
+    bool prep_A, prep_B;   // whether A / B are converted into the workspace
+    int64_t ldat, ldbp;    // leading dimensions of the operands the sketch reads
+};
+
+// ---- launchers (sketch.cu / sketch_f64.cu / finish.cu) ----
+cudaError_t launch_prep_A(const void *A, int64_t lda, int transA, int dtype, int prec,
+                          int64_t m, int64_t k, void *At, int64_t ldat, cudaStream_t s);
+cudaError_t launch_prep_B(const void *B, int64_t ldb, int dtype, int prec,
+                          int64_t k, int64_t p, void *Bp, int64_t ldbp, cudaStream_t s);
+cudaError_t launch_sketch_f32(const SketchPlan &pl, const float *At, const float *Bp,
+                              int64_t m, int64_t k, int64_t p, int d, const HashParams &hp,
+                              double *partial, cudaStream_t s);
+cudaError_t launch_sketch_f64(const SketchPlan &pl, const double *At, const double *Bp,
+                              int64_t m, int64_t k, int64_t p, int d, const HashParams &hp,
+                              double *partial, cudaStream_t s);
+cudaError_t launch_finish(const double *partial, int nchunks, int d, int L, double *Z,
+                          double *R, cudaStream_t s);
+int sketch_threads_f32(int Llo);
+int sketch_threads_f64(int Llo);
+size_t sketch_smem_f32(int Llo);
+size_t sketch_smem_f64(int Llo);
+
+// ---- extraction (extract.cu) ----
+cudaError_t launch_hash_tables(const HashParams &hp, int d, int L, int64_t m, int64_t p,
+                               uint32_t *H1, uint32_t *H2, cudaStream_t s);
+cudaError_t launch_extract(const double *R, const uint32_t *H1, const uint32_t *H2, int d,
+                           int L, int64_t m, int64_t p, int reduce, double *C, int64_t ldc,
+                           cudaStream_t s);
+cudaError_t launch_hh_count(const double *R, const uint32_t *H1, const uint32_t *H2,
+                            const double *C, int64_t ldc, int d, int L, int64_t m, int64_t p,
+                            int reduce, double tau, int64_t tile, int64_t ntiles,
+                            int64_t *counts, cudaStream_t s);
+cudaError_t launch_hh_scan(int64_t *counts, int64_t ntiles, cudaStream_t s);
+cudaError_t launch_hh_write(const double *R, const uint32_t *H1, const uint32_t *H2,
+                            const double *C, int64_t ldc, int d, int L, int64_t m, int64_t p,
+                            int reduce, double tau, int64_t tile, int64_t ntiles,
+                            const int64_t *offsets, int32_t *I, int32_t *J, double *V,
+                            int64_t capacity, cudaStream_t s);
+cudaError_t launch_mean_pairs(const double *R, const HashParams &hp, int d, int L, int64_t P,
+                              const int32_t *I, const int32_t *J, double *out, cudaStream_t s);
+
+}  // namespace cmm

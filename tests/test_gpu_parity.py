@@ -1,0 +1,184 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 oracle.
+
+Sketch: R_gpu vs oracle Compress on the same input values (widened to FP64),
+max |R_gpu - R_orc| / sum_t ||A[:,t]|| ||B[t,:]|| within 1e-12 (FP64
+butterflies) or 1e-5 (FP32 butterflies); exactly equal on +-1 inputs.
+Decompress / heavy hitters / mean at pairs: given the SAME R, the GPU result
+is bit-identical to the oracle's (the median is a selection, the mean uses the
+same operation order), and the heavy-hitter lists are identical.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as orc
+from paper_2601_09477_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-12, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def cmm():
+    assert torch.cuda.is_available(), "these tests need a CUDA GPU"
+    from paper_2601_09477_gb300 import cmm as mod
+    return mod
+
+
+def _norm_scale(A64, B64):
+    # sum_t ||A[:, t]||_2 ||B[t, :]||_2
+    return float(np.sum(np.linalg.norm(A64, axis=0) * np.linalg.norm(B64, axis=1)))
+
+
+def _dev(x, dtype):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(device="cuda", dtype=dtype)
+
+
+SHAPES = [
+    # (m, k, p, log2b, d)
+    (100, 37, 90, 6, 3),
+    (300, 129, 257, 12, 5),
+    (513, 300, 411, 13, 3),
+    (700, 260, 650, 14, 3),
+    (1000, 200, 900, 15, 3),     # two FP32 slices (four FP64 slices)
+    (517, 97, 333, 17, 2),       # 8 / 16 slices, even d
+    (64, 1000, 50, 3, 1),        # tiny transform, many inner indices
+    (1, 5, 1, 1, 1),             # b = 2
+    (33, 70, 2, 5, 4),
+]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_sketch_matches_oracle(cmm, prec, shape):
+    m, k, p, L, d = shape
+    g = np.random.default_rng(m * 7 + k * 3 + p + L)
+    A = g.standard_normal((m, k))
+    B = g.standard_normal((k, p))
+    h = cmm.make_hashes(1000 + L, d, L)
+    R = cmm.sketch(_dev(A, torch.float64), _dev(B, torch.float64), h, prec=prec).cpu().numpy()
+    Ro = orc.compress(A, B, h.params, L, nthreads=8)
+    err = np.abs(R - Ro).max() / _norm_scale(A, B)
+    assert err <= TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("transA", [False, True])
+def test_sketch_dtypes_and_layouts(cmm, prec, dtype, transA):
+    m, k, p, L, d = 300, 150, 280, 11, 3
+    g = np.random.default_rng(5)
+    A = g.standard_normal((m, k))
+    B = g.standard_normal((k, p))
+    At = _dev(A.T if transA else A, dtype)
+    Bt = _dev(B, dtype)
+    # the oracle sees the same (rounded) values, widened to FP64
+    A_in = At.double().cpu().numpy()
+    B_in = Bt.double().cpu().numpy()
+    h = cmm.make_hashes(77, d, L)
+    R = cmm.sketch(At, Bt, h, prec=prec, transA=transA).cpu().numpy()
+    Ro = orc.compress(A_in, B_in, h.params, L, transA=transA, nthreads=8)
+    scale = _norm_scale(A_in.T if transA else A_in, B_in)
+    assert np.abs(R - Ro).max() / scale <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_sketch_pm1_exact(cmm, prec):
+    A, B, _ = wl.planted_pm1(n=512, pairs=8, seed=3)
+    h = cmm.make_hashes(5, 5, 13)
+    R = cmm.sketch(_dev(A, torch.float64), _dev(B, torch.float64), h, prec=prec).cpu().numpy()
+    Ro = orc.compress(A, B, h.params, 13, nthreads=8)
+    assert np.array_equal(R, Ro)
+
+
+def test_sketch_empty_inner_dimension(cmm):
+    h = cmm.make_hashes(1, 3, 8)
+    A = torch.zeros((20, 0), dtype=torch.float64, device="cuda")
+    B = torch.zeros((0, 30), dtype=torch.float64, device="cuda")
+    R = cmm.sketch(A, B, h, prec="f32")
+    assert torch.count_nonzero(R).item() == 0
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 7, 9, 11, 16, 17])
+@pytest.mark.parametrize("reduce", ["median", "mean"])
+def test_extract_bitwise_given_R(cmm, d, reduce):
+    m, p, L = 67, 301, 9
+    g = np.random.default_rng(d)
+    R = g.standard_normal((d, 1 << L)) * 10
+    R[0, :7] = 0.0   # exercise signed zeros
+    h = cmm.make_hashes(40 + d, d, L)
+    C = cmm.extract(_dev(R, torch.float64), h, m, p, reduce=reduce).cpu().numpy()
+    Co = orc.extract(R, h.params, m, p, orc.MEDIAN if reduce == "median" else orc.MEAN)
+    assert np.array_equal(C, Co)
+
+
+@pytest.mark.parametrize("d", [3, 4, 9])
+def test_heavy_hitters_given_R(cmm, d):
+    m, p, L = 150, 230, 8
+    g = np.random.default_rng(100 + d)
+    R = g.standard_normal((d, 1 << L)) * 3
+    h = cmm.make_hashes(7 + d, d, L)
+    Rt = _dev(R, torch.float64)
+    I, J, V = cmm.heavy_hitters(Rt, h, m, p, tau=2.0)
+    Io, Jo, Vo = orc.heavy_hitters(R, h.params, m, p, 2.0)
+    assert np.array_equal(I.cpu().numpy(), Io)
+    assert np.array_equal(J.cpu().numpy(), Jo)
+    assert np.array_equal(V.cpu().numpy(), Vo)
+    # from the dense estimate
+    C = cmm.extract(Rt, h, m, p)
+    I2, J2, V2 = cmm.threshold(C, 2.0)
+    assert np.array_equal(I2.cpu().numpy(), Io) and np.array_equal(V2.cpu().numpy(), Vo)
+
+
+def test_heavy_hitters_capacity(cmm):
+    m, p, L, d = 40, 50, 6, 3
+    R = np.random.default_rng(1).standard_normal((d, 1 << L)) * 3
+    h = cmm.make_hashes(3, d, L)
+    Rt = _dev(R, torch.float64)
+    Io, Jo, Vo = orc.heavy_hitters(R, h.params, m, p, 1.0)
+    assert len(Io) > 10
+    with pytest.raises(cmm.CmmError) as ei:
+        cmm.heavy_hitters(Rt, h, m, p, tau=1.0, capacity=10)
+    assert ei.value.code == cmm.ERR_CAPACITY
+    I, J, V = cmm.heavy_hitters(Rt, h, m, p, tau=1.0, capacity=len(Io))
+    assert np.array_equal(I.cpu().numpy(), Io)
+    I, J, V = cmm.heavy_hitters(Rt, h, m, p, tau=1e9)
+    assert I.numel() == 0
+
+
+def test_mean_pairs_bitwise(cmm):
+    d, L = 5, 10
+    g = np.random.default_rng(9)
+    R = g.standard_normal((d, 1 << L))
+    h = cmm.make_hashes(11, d, L)
+    I = g.integers(0, 5000, 999).astype(np.int32)
+    J = g.integers(0, 7000, 999).astype(np.int32)
+    out = cmm.mean_pairs(_dev(R, torch.float64), h, torch.from_numpy(I), torch.from_numpy(J))
+    assert np.array_equal(out.cpu().numpy(), orc.mean_at_pairs(R, h.params, I, J))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_multiply_orthogonal_sparse_256(cmm, prec):
+    # n = 256, b = 2^12, d = 5, heavy-hitter threshold 5 (A B = S exactly)
+    A, B, S = wl.orthogonal_sparse(seed=1001)
+    h = cmm.make_hashes(2001, 5, 12)
+    R = torch.empty((5, 4096), dtype=torch.float64, device="cuda")
+    C = cmm.multiply(_dev(A, torch.float64), _dev(B, torch.float64), h, prec=prec, R=R)
+    Rg = R.cpu().numpy()
+    Ro = orc.compress(A, B, h.params, 12, nthreads=8)
+    dR = np.abs(Rg - Ro).max()
+    assert dR / _norm_scale(A, B) <= TOL[prec]
+    Co = orc.extract(Ro, h.params, 256, 256)
+    # the median is 1-Lipschitz in the sup norm of R
+    assert np.abs(C.cpu().numpy() - Co).max() <= dR
+    # heavy hitters: identical outside a band of |C| around tau
+    I, J, V = cmm.threshold(C, 5.0)
+    got = set(zip(I.cpu().tolist(), J.cpu().tolist()))
+    Io, Jo, _ = orc.heavy_hitters(Ro, h.params, 256, 256, 5.0)
+    want = set(zip(Io.tolist(), Jo.tolist()))
+    band = {(i, j) for i in range(256) for j in range(256) if abs(abs(Co[i, j]) - 5.0) <= max(1e-9 * 5, 2 * dR)}
+    assert got - band == want - band
+    # and the planted entries are recovered
+    si, sj = np.nonzero(np.abs(S) >= 5.0)
+    assert set(zip(si.tolist(), sj.tolist())) <= got

@@ -1,0 +1,106 @@
+"""CPU-side checks of libcmm: the library loads, exports every entry point that
+include/cmm.h declares, its host-side hash generation agrees bit for bit with
+the oracle's, and argument errors come back before anything is launched (no
+GPU is touched here)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "cmm.h")
+
+
+@pytest.fixture(scope="module")
+def cmm():
+    from paper_2601_09477_gb300 import build
+    build.build()
+    from paper_2601_09477_gb300 import cmm as mod
+    return mod
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cmm_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for n in ["cmm_make_hashes", "cmm_sketch", "cmm_extract", "cmm_heavy_hitters",
+              "cmm_threshold", "cmm_multiply", "cmm_mean_pairs", "cmm_last_error"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(cmm):
+    lib = ctypes.CDLL(cmm.LIB_PATH)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert "sm_103a" in cmm.version()
+
+
+@pytest.mark.parametrize("seed,d", [(0, 1), (1, 5), (2009, 9), (2**64 - 1, 64)])
+def test_make_hashes_matches_oracle(cmm, seed, d):
+    h = cmm.make_hashes(seed, d, 10)
+    assert np.array_equal(h.params, orc.draw_hashes(seed, d))
+
+
+def test_argument_errors_before_launch(cmm):
+    lib = cmm.lib
+    params = np.zeros((3, 8), dtype=np.uint64)
+    hs = cmm.Hashes(3, 8, params)
+    dummy = ctypes.c_void_p(256)   # never dereferenced: every call below fails its checks
+    # bad d / log2b
+    assert lib.cmm_make_hashes(1, 0, params.ctypes.data) == cmm.ERR_RANGE
+    assert lib.cmm_make_hashes(1, 65, params.ctypes.data) == cmm.ERR_RANGE
+    assert lib.cmm_make_hashes(1, 3, None) == cmm.ERR_ARG
+    bad = cmm.Hashes(3, 25, params)
+    assert lib.cmm_sketch(dummy, 4, 0, dummy, 4, cmm.F32, 4, 4, 4, bad.ref, cmm.PREC_F32,
+                          dummy, dummy, 1 << 30, None) == cmm.ERR_RANGE
+    # null operands, bad dtype, bad leading dimension, bad precision
+    assert lib.cmm_sketch(None, 4, 0, dummy, 4, cmm.F32, 4, 4, 4, hs.ref, cmm.PREC_F32,
+                          dummy, dummy, 1 << 30, None) == cmm.ERR_ARG
+    assert lib.cmm_sketch(dummy, 4, 0, dummy, 4, 7, 4, 4, 4, hs.ref, cmm.PREC_F32,
+                          dummy, dummy, 1 << 30, None) == cmm.ERR_ARG
+    assert lib.cmm_sketch(dummy, 3, 0, dummy, 4, cmm.F32, 4, 4, 4, hs.ref, cmm.PREC_F32,
+                          dummy, dummy, 1 << 30, None) == cmm.ERR_ARG
+    assert lib.cmm_sketch(dummy, 4, 0, dummy, 4, cmm.F32, 4, 4, 4, hs.ref, 9,
+                          dummy, dummy, 1 << 30, None) == cmm.ERR_ARG
+    assert "precision" in lib.cmm_last_error().decode()
+    # m, p must be < 2^31 (32-bit hash keys)
+    assert lib.cmm_sketch(dummy, 1 << 31, 1, dummy, 4, cmm.F32, 1 << 31, 4, 4, hs.ref,
+                          cmm.PREC_F32, dummy, dummy, 1 << 30, None) == cmm.ERR_RANGE
+    # workspace: null, misaligned, too small
+    need = lib.cmm_sketch_workspace_bytes(64, 64, 64, 3, 8, cmm.F64, cmm.PREC_F32, 0)
+    assert need > 0
+    assert lib.cmm_sketch(dummy, 64, 0, dummy, 64, cmm.F64, 64, 64, 64, hs.ref, cmm.PREC_F32,
+                          dummy, None, 0, None) == cmm.ERR_WORKSPACE
+    assert lib.cmm_sketch(dummy, 64, 0, dummy, 64, cmm.F64, 64, 64, 64, hs.ref, cmm.PREC_F32,
+                          dummy, ctypes.c_void_p(257), need, None) == cmm.ERR_WORKSPACE
+    assert lib.cmm_sketch(dummy, 64, 0, dummy, 64, cmm.F64, 64, 64, 64, hs.ref, cmm.PREC_F32,
+                          dummy, dummy, need - 1, None) == cmm.ERR_WORKSPACE
+    # extraction / heavy hitters
+    assert lib.cmm_extract(dummy, hs.ref, 4, 4, 5, dummy, 4, dummy, 1 << 20, None) == cmm.ERR_ARG
+    assert lib.cmm_extract(dummy, hs.ref, 4, 4, 0, dummy, 3, dummy, 1 << 20, None) == cmm.ERR_ARG
+    cnt = ctypes.c_int64(0)
+    assert lib.cmm_heavy_hitters(dummy, hs.ref, 4, 4, 0, 1.0, dummy, dummy, dummy, -1,
+                                 ctypes.byref(cnt), dummy, 1 << 20, None) == cmm.ERR_ARG
+    assert lib.cmm_heavy_hitters(dummy, hs.ref, 4, 4, 0, 1.0, dummy, dummy, dummy, 4,
+                                 None, dummy, 1 << 20, None) == cmm.ERR_ARG
+    assert lib.cmm_mean_pairs(dummy, hs.ref, -1, dummy, dummy, dummy, None) == cmm.ERR_ARG
+
+
+def test_workspace_queries_scale(cmm):
+    lib = cmm.lib
+    small = lib.cmm_sketch_workspace_bytes(256, 256, 256, 5, 12, cmm.F64, cmm.PREC_F64, 0)
+    big = lib.cmm_sketch_workspace_bytes(8192, 8192, 8192, 9, 16, cmm.F64, cmm.PREC_F32, 1)
+    assert 0 < small < big
+    assert small % 256 == 0 and big % 256 == 0
+    assert lib.cmm_sketch_workspace_bytes(8, 8, 8, 0, 4, cmm.F32, cmm.PREC_F32, 0) == 0
+    assert lib.cmm_extract_workspace_bytes(100, 100, 5) >= 5 * 200 * 4
+    assert lib.cmm_multiply_workspace_bytes(256, 256, 256, 5, 12, cmm.F64, cmm.PREC_F64, 0) >= \
+        5 * 4096 * 8
