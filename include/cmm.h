@@ -142,6 +142,26 @@ int cmm_multiply(const void *A, int64_t lda, int32_t transA, const void *B, int6
                  int32_t prec, int32_t reduce, double *C, int64_t ldc, double *R,
                  void *ws, size_t ws_bytes, void *stream);
 
+/* Bytes of `ws` (device) needed by cmm_multiply_host with room for a
+ * heavy-hitter list of `capacity` entries. */
+size_t cmm_multiply_host_workspace_bytes(int64_t m, int64_t k, int64_t p, int32_t d,
+                                         int32_t log2b, int32_t dtype, int32_t prec,
+                                         int32_t transA, int64_t capacity);
+
+/* cmm_multiply for operands in HOST memory (pinned memory gives full copy
+ * speed; pageable memory works too): A and B (host, `dtype`, leading
+ * dimensions as in cmm_sketch) are copied into `ws`, the estimate is computed
+ * there, C (host, m x p FP64, ldc >= p; may be NULL) receives it, and when
+ * `count` is not NULL the heavy hitters |C[i][j]| >= tau in (i, j) order are
+ * copied to I, J, V (host, `capacity` entries; *count = total found).
+ * Synchronous: returns once the results are in host memory.  Errors: as
+ * cmm_multiply, plus CMM_ERR_CAPACITY as in cmm_threshold. */
+int cmm_multiply_host(const void *A, int64_t lda, int32_t transA, const void *B, int64_t ldb,
+                      int32_t dtype, int64_t m, int64_t k, int64_t p, const cmm_hashes *hs,
+                      int32_t prec, int32_t reduce, double *C, int64_t ldc, double tau,
+                      int64_t capacity, int32_t *I, int32_t *J, double *V, int64_t *count,
+                      void *ws, size_t ws_bytes, void *stream);
+
 /* Mean estimator at a list of P pairs (the differentiable form):
  * out[q] = (1/d) sum_r s1_r(I[q]) s2_r(J[q]) R_r[h1_r(I[q]) XOR h2_r(J[q])].
  * I, J: device int32 (0 <= I < m, 0 <= J < p, not checked on the device);
@@ -150,6 +170,19 @@ int cmm_multiply(const void *A, int64_t lda, int32_t transA, const void *B, int6
  * Errors: CMM_ERR_ARG, CMM_ERR_RANGE, CMM_ERR_CUDA. */
 int cmm_mean_pairs(const double *R, const cmm_hashes *hs, int64_t P, const int32_t *I,
                    const int32_t *J, double *out, void *stream);
+
+/* Launch tracing (the library's profiling hook).  While enabled, every
+ * kernel launch the library makes is bracketed by CUDA events recorded on the
+ * caller's stream.  cmm_trace_enable(1) clears earlier records and starts
+ * recording; cmm_trace_enable(0) stops.  cmm_trace_read waits for the recorded
+ * events and returns, per kernel name (at most max_entries of them, each name a
+ * NUL-terminated string in a 32-byte slot of `names`, host), the number of
+ * launches and the summed device time in ms; *n_out (host) is the number of
+ * distinct names.  Tracing adds two event records per launch.  The paper has
+ * no counterpart (it reports wall-clock times only, Sec. 5.4). */
+int cmm_trace_enable(int32_t on);
+int cmm_trace_read(int32_t max_entries, char *names, int64_t *launches, double *total_ms,
+                   int32_t *n_out);
 
 /* Last error message of the calling host thread ("" when none). */
 const char *cmm_last_error(void);

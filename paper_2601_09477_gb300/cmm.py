@@ -72,7 +72,13 @@ def _load() -> ctypes.CDLL:
         "cmm_multiply_workspace_bytes": (sz, [i64, i64, i64, i32, i32, i32, i32, i32]),
         "cmm_multiply": (ctypes.c_int, [P, i64, i32, P, i64, i32, i64, i64, i64, H, i32, i32,
                                         P, i64, P, P, sz, P]),
+        "cmm_multiply_host_workspace_bytes": (sz, [i64, i64, i64, i32, i32, i32, i32, i32, i64]),
+        "cmm_multiply_host": (ctypes.c_int, [P, i64, i32, P, i64, i32, i64, i64, i64, H, i32, i32,
+                                             P, i64, f64, i64, P, P, P,
+                                             ctypes.POINTER(ctypes.c_int64), P, sz, P]),
         "cmm_mean_pairs": (ctypes.c_int, [P, H, i64, P, P, P, P]),
+        "cmm_trace_enable": (ctypes.c_int, [i32]),
+        "cmm_trace_read": (ctypes.c_int, [i32, P, P, P, P]),
         "cmm_last_error": (ctypes.c_char_p, []),
         "cmm_version": (ctypes.c_char_p, []),
     }
@@ -88,6 +94,25 @@ lib = _load()
 
 def version() -> str:
     return lib.cmm_version().decode()
+
+
+def trace_enable(on: bool = True):
+    """Start (clearing earlier records) or stop the library's launch tracing."""
+    _check(lib.cmm_trace_enable(int(bool(on))))
+
+
+def trace_read(max_entries: int = 64) -> dict:
+    """{kernel name: (launches, summed device ms)} of the launches traced so far."""
+    names = ctypes.create_string_buffer(32 * max_entries)
+    launches = (ctypes.c_int64 * max_entries)()
+    total = (ctypes.c_double * max_entries)()
+    n = ctypes.c_int32(0)
+    _check(lib.cmm_trace_read(max_entries, names, launches, total, ctypes.byref(n)))
+    out = {}
+    for q in range(min(n.value, max_entries)):
+        nm = names.raw[32 * q: 32 * (q + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (int(launches[q]), float(total[q]))
+    return out
 
 
 def _check(rc: int):
@@ -239,6 +264,49 @@ def multiply(A: torch.Tensor, B: torch.Tensor, h: Hashes, prec: str = "f32",
                             R.data_ptr() if R is not None else None, ws.data_ptr(),
                             ws.numel(), _stream(stream)))
     return C
+
+
+def multiply_host_workspace_bytes(m, k, p, h: Hashes, dtype, prec: str = "f32",
+                                  transA=False, capacity: int = 0) -> int:
+    return int(lib.cmm_multiply_host_workspace_bytes(m, k, p, h.d, h.log2b, _DTYPE[dtype],
+                                                     _PREC[prec], int(transA), int(capacity)))
+
+
+def multiply_host(A: torch.Tensor, B: torch.Tensor, h: Hashes, prec: str = "f32",
+                  reduce: str = "median", transA: bool = False, out: torch.Tensor | None = None,
+                  tau: float | None = None, capacity: int = 0, hh_out=None,
+                  ws: torch.Tensor | None = None, device="cuda", stream=None):
+    """cmm_multiply on HOST tensors (pin them for full copy speed): returns the
+    host estimate C and, when ``tau`` is given, the host heavy-hitter list
+    (I, J, V) with |C| >= tau.  Synchronous."""
+    if A.device.type != "cpu" or B.device.type != "cpu":
+        raise ValueError("multiply_host takes host tensors")
+    m, k, p, dt = _operands(A, B, transA)
+    pr = _PREC[prec]
+    cap = int(capacity) if tau is not None else 0
+    need = lib.cmm_multiply_host_workspace_bytes(m, k, p, h.d, h.log2b, dt, pr, int(transA), cap)
+    if ws is None or ws.numel() < need:
+        ws = _workspace(need, device)
+    C = out if out is not None else torch.empty((m, p), dtype=torch.float64)
+    cnt = ctypes.c_int64(0)
+    if tau is not None:
+        if hh_out is None:
+            hh_out = (torch.empty(max(cap, 1), dtype=torch.int32),
+                      torch.empty(max(cap, 1), dtype=torch.int32),
+                      torch.empty(max(cap, 1), dtype=torch.float64))
+        Ih, Jh, Vh = hh_out
+        ptrs = (Ih.data_ptr(), Jh.data_ptr(), Vh.data_ptr(), ctypes.byref(cnt))
+    else:
+        ptrs = (None, None, None, None)
+    _check(lib.cmm_multiply_host(A.data_ptr(), max(A.stride(0), 1), int(transA), B.data_ptr(),
+                                 max(B.stride(0), 1), dt, m, k, p, h.ref, pr, _REDUCE[reduce],
+                                 C.data_ptr(), max(C.stride(0), 1),
+                                 float(tau) if tau is not None else 0.0, cap, *ptrs,
+                                 ws.data_ptr(), ws.numel(), _stream(stream)))
+    if tau is None:
+        return C, None
+    n = cnt.value
+    return C, (hh_out[0][:n], hh_out[1][:n], hh_out[2][:n])
 
 
 def mean_pairs(R: torch.Tensor, h: Hashes, I: torch.Tensor, J: torch.Tensor,

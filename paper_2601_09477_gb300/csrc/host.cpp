@@ -5,7 +5,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <vector>
 
 #include "cmm_internal.h"
 
@@ -28,6 +30,52 @@ int fail(int code, const char *fmt, ...) {
 int cuda_fail(cudaError_t e, const char *where) {
     return fail(CMM_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
+
+// ---- launch tracing: CUDA events around every kernel launch while enabled ----
+struct TraceRec {
+    const char *name;
+    int launches;
+    cudaEvent_t a, b;
+};
+std::mutex g_tr_mu;
+bool g_tr_on = false;
+std::vector<TraceRec> g_tr;
+std::vector<cudaEvent_t> g_ev_pool;
+
+cudaEvent_t tr_event() {
+    cudaEvent_t e = nullptr;
+    if (!g_ev_pool.empty()) {
+        e = g_ev_pool.back();
+        g_ev_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        e = nullptr;
+    }
+    return e;
+}
+
+// RAII span: records an event on `s` at construction and at destruction
+struct Span {
+    bool on = false;
+    TraceRec rec{};
+    cudaStream_t s;
+    Span(const char *name, cudaStream_t st, int launches = 1) : s(st) {
+        std::lock_guard<std::mutex> lk(g_tr_mu);
+        if (!g_tr_on) return;
+        rec.name = name;
+        rec.launches = launches;
+        rec.a = tr_event();
+        rec.b = tr_event();
+        if (!rec.a || !rec.b) return;
+        on = cudaEventRecord(rec.a, s) == cudaSuccess;
+    }
+    ~Span() {
+        if (!on) return;
+        cudaEventRecord(rec.b, s);
+        std::lock_guard<std::mutex> lk(g_tr_mu);
+        g_tr.push_back(rec);
+    }
+};
 
 constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
@@ -189,25 +237,33 @@ int run_sketch(const void *A, int64_t lda, int transA, const void *B, int64_t ld
     const void *At = A, *Bp = B;
     cudaError_t e;
     if (pl.prep_A && m > 0 && k > 0) {
+        Span sp("prep_A", s);
         e = launch_prep_A(A, lda, transA, dtype, prec, m, k, base + pl.off_At, pl.ldat, s);
         if (e != cudaSuccess) return cuda_fail(e, "prep A");
         At = base + pl.off_At;
     }
     if (pl.prep_B && p > 0 && k > 0) {
+        Span sp("prep_B", s);
         e = launch_prep_B(B, ldb, dtype, prec, k, p, base + pl.off_Bp, pl.ldbp, s);
         if (e != cudaSuccess) return cuda_fail(e, "prep B");
         Bp = base + pl.off_Bp;
     }
     double *partial = reinterpret_cast<double *>(base + pl.off_partial);
     double *Z = reinterpret_cast<double *>(base + pl.off_Z);
-    if (prec == CMM_PREC_F64)
-        e = launch_sketch_f64(pl, (const double *)At, (const double *)Bp, m, k, p, hs->d, hp,
-                              partial, s);
-    else
-        e = launch_sketch_f32(pl, (const float *)At, (const float *)Bp, m, k, p, hs->d, hp,
-                              partial, s);
+    {
+        Span sp(prec == CMM_PREC_F64 ? "sketch_f64" : "sketch_f32", s);
+        if (prec == CMM_PREC_F64)
+            e = launch_sketch_f64(pl, (const double *)At, (const double *)Bp, m, k, p, hs->d, hp,
+                                  partial, s);
+        else
+            e = launch_sketch_f32(pl, (const float *)At, (const float *)Bp, m, k, p, hs->d, hp,
+                                  partial, s);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "sketch kernel");
-    e = launch_finish(partial, pl.nchunks, hs->d, hs->log2b, Z, R, s);
+    {
+        Span sp("finish", s, 2);
+        e = launch_finish(partial, pl.nchunks, hs->d, hs->log2b, Z, R, s);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "finish kernels");
     return CMM_OK;
 }
@@ -218,9 +274,16 @@ int run_extract(const double *R, const cmm_hashes *hs, int64_t m, int64_t p, int
     HashParams hp;
     fill_params(hs, hp);
     ExtractWs ew = carve_extract(ws, m, p, hs->d);
-    cudaError_t e = launch_hash_tables(hp, hs->d, hs->log2b, m, p, ew.H1, ew.H2, s);
+    cudaError_t e;
+    {
+        Span sp("hash_tables", s);
+        e = launch_hash_tables(hp, hs->d, hs->log2b, m, p, ew.H1, ew.H2, s);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "hash tables");
-    e = launch_extract(R, ew.H1, ew.H2, hs->d, hs->log2b, m, p, reduce, C, ldc, s);
+    {
+        Span sp("extract", s);
+        e = launch_extract(R, ew.H1, ew.H2, hs->d, hs->log2b, m, p, reduce, C, ldc, s);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "extract kernel");
     return CMM_OK;
 }
@@ -235,12 +298,19 @@ int run_hh(const double *R, const cmm_hashes *hs, const double *C, int64_t ldc, 
     if (!C) {
         HashParams hp;
         fill_params(hs, hp);
+        Span sp("hash_tables", s);
         e = launch_hash_tables(hp, d, L, m, p, ew.H1, ew.H2, s);
         if (e != cudaSuccess) return cuda_fail(e, "hash tables");
     }
-    e = launch_hh_count(R, ew.H1, ew.H2, C, ldc, d, L, m, p, reduce, tau, 1, m, ew.counts, s);
+    {
+        Span sp(C ? "hh_count_dense" : "hh_count", s);
+        e = launch_hh_count(R, ew.H1, ew.H2, C, ldc, d, L, m, p, reduce, tau, 1, m, ew.counts, s);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter count");
-    e = launch_hh_scan(ew.counts, m, s);
+    {
+        Span sp("hh_scan", s);
+        e = launch_hh_scan(ew.counts, m, s);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter scan");
     int64_t total = 0;
     e = cudaMemcpyAsync(&total, ew.counts + 2 * m, sizeof total, cudaMemcpyDeviceToHost, s);
@@ -249,8 +319,11 @@ int run_hh(const double *R, const cmm_hashes *hs, const double *C, int64_t ldc, 
     if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter count sync");
     *count = total;
     if (total > 0 && capacity > 0) {
-        e = launch_hh_write(R, ew.H1, ew.H2, C, ldc, d, L, m, p, reduce, tau, 1, m,
-                            ew.counts + m, I, J, V, capacity, s);
+        {
+            Span sp(C ? "hh_write_dense" : "hh_write", s);
+            e = launch_hh_write(R, ew.H1, ew.H2, C, ldc, d, L, m, p, reduce, tau, 1, m,
+                                ew.counts + m, I, J, V, capacity, s);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter write");
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter write sync");
@@ -277,6 +350,55 @@ extern "C" {
 const char *cmm_last_error(void) { return g_err.c_str(); }
 
 const char *cmm_version(void) { return "cmm 0.1.0 (sm_103a)"; }
+
+int cmm_trace_enable(int32_t on) {
+    g_err.clear();
+    std::lock_guard<std::mutex> lk(g_tr_mu);
+    if (on) {
+        for (auto &r : g_tr) {
+            g_ev_pool.push_back(r.a);
+            g_ev_pool.push_back(r.b);
+        }
+        g_tr.clear();
+    }
+    g_tr_on = on != 0;
+    return CMM_OK;
+}
+
+int cmm_trace_read(int32_t max_entries, char *names, int64_t *launches, double *total_ms,
+                   int32_t *n_out) {
+    g_err.clear();
+    if (!n_out || (max_entries > 0 && (!names || !launches || !total_ms)))
+        return fail(CMM_ERR_ARG, "null pointer");
+    std::lock_guard<std::mutex> lk(g_tr_mu);
+    std::vector<std::string> keys;
+    std::vector<int64_t> cnt;
+    std::vector<double> tot;
+    for (auto &r : g_tr) {
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e != cudaSuccess) return cuda_fail(e, "trace event");
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) return cuda_fail(e, "trace elapsed");
+        size_t q = 0;
+        while (q < keys.size() && keys[q] != r.name) ++q;
+        if (q == keys.size()) {
+            keys.push_back(r.name);
+            cnt.push_back(0);
+            tot.push_back(0.0);
+        }
+        cnt[q] += r.launches;
+        tot[q] += ms;
+    }
+    const int n = (int)keys.size();
+    for (int q = 0; q < n && q < max_entries; ++q) {
+        std::snprintf(names + 32 * q, 32, "%s", keys[q].c_str());
+        launches[q] = cnt[q];
+        total_ms[q] = tot[q];
+    }
+    *n_out = n;
+    return CMM_OK;
+}
 
 int cmm_make_hashes(uint64_t seed, int32_t d, uint64_t *params) {
     g_err.clear();
@@ -407,6 +529,103 @@ int cmm_multiply(const void *A, int64_t lda, int32_t transA, const void *B, int6
     return run_extract(Rw, hs, m, p, reduce, C, ldc, scratch, s);
 }
 
+size_t cmm_multiply_host_workspace_bytes(int64_t m, int64_t k, int64_t p, int32_t d,
+                                         int32_t log2b, int32_t dtype, int32_t prec,
+                                         int32_t transA, int64_t capacity) {
+    const size_t mw = cmm_multiply_workspace_bytes(m, k, p, d, log2b, dtype, prec, transA);
+    if (!mw || capacity < 0) return 0;
+    const size_t es = dtype_size(dtype);
+    return align_up((size_t)m * k * es) + align_up((size_t)k * p * es) +
+           align_up((size_t)m * p * sizeof(double)) +
+           align_up((size_t)capacity * (2 * sizeof(int32_t) + sizeof(double))) + mw;
+}
+
+int cmm_multiply_host(const void *A, int64_t lda, int32_t transA, const void *B, int64_t ldb,
+                      int32_t dtype, int64_t m, int64_t k, int64_t p, const cmm_hashes *hs,
+                      int32_t prec, int32_t reduce, double *C, int64_t ldc, double tau,
+                      int64_t capacity, int32_t *I, int32_t *J, double *V, int64_t *count,
+                      void *ws, size_t ws_bytes, void *stream) {
+    g_err.clear();
+    int rc = check_hashes(hs);
+    if (rc) return rc;
+    rc = check_operands(A, lda, transA, B, ldb, dtype, m, k, p, prec);
+    if (rc) return rc;
+    if (prec == CMM_PREC_BF16TC)
+        return fail(CMM_ERR_ARG, "precision BF16TC is not available in this build");
+    if (reduce != CMM_MEDIAN && reduce != CMM_MEAN) return fail(CMM_ERR_ARG, "bad reduce %d", reduce);
+    if (C && ldc < p) return fail(CMM_ERR_ARG, "ldc = %lld < p", (long long)ldc);
+    if (count && capacity < 0) return fail(CMM_ERR_ARG, "negative capacity");
+    if (count && capacity > 0 && (!I || !J || !V)) return fail(CMM_ERR_ARG, "I, J or V is NULL");
+    const int64_t cap = count ? capacity : 0;
+    const size_t need = cmm_multiply_host_workspace_bytes(m, k, p, hs->d, hs->log2b, dtype, prec,
+                                                          transA, cap);
+    rc = check_ws(ws, ws_bytes, need);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t es = dtype_size(dtype);
+    char *base = static_cast<char *>(ws);
+    char *dA = base;
+    base += align_up((size_t)m * k * es);
+    char *dB = base;
+    base += align_up((size_t)k * p * es);
+    double *dC = reinterpret_cast<double *>(base);
+    base += align_up((size_t)m * p * sizeof(double));
+    int32_t *dI = reinterpret_cast<int32_t *>(base);
+    int32_t *dJ = dI + cap;
+    double *dV = reinterpret_cast<double *>(base + align_up((size_t)cap * 2 * sizeof(int32_t)));
+    base += align_up((size_t)cap * (2 * sizeof(int32_t) + sizeof(double)));
+    // A as stored: m x k (transA = 0) or k x m (transA = 1), compacted on the device
+    const int64_t arows = transA ? k : m, acols = transA ? m : k;
+    cudaError_t e;
+    if (arows > 0 && acols > 0) {
+        Span sp("h2d_A", s, 0);
+        e = cudaMemcpy2DAsync(dA, acols * es, A, lda * es, acols * es, arows,
+                              cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "copy A to device");
+    }
+    if (k > 0 && p > 0) {
+        Span sp("h2d_B", s, 0);
+        e = cudaMemcpy2DAsync(dB, p * es, B, ldb * es, p * es, k, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "copy B to device");
+    }
+    const size_t rbytes = align_up((size_t)hs->d * (size_t(1) << hs->log2b) * sizeof(double));
+    double *Rw = reinterpret_cast<double *>(base);
+    void *scratch = base + rbytes;
+    rc = run_sketch(dA, acols > 0 ? acols : 1, transA, dB, p > 0 ? p : 1, dtype, m, k, p, hs, prec,
+                    Rw, scratch, s);
+    if (rc) return rc;
+    rc = run_extract(Rw, hs, m, p, reduce, dC, p, scratch, s);
+    if (rc) return rc;
+    if (C && m > 0 && p > 0) {
+        Span sp("d2h_C", s, 0);
+        e = cudaMemcpy2DAsync(C, ldc * sizeof(double), dC, p * sizeof(double), p * sizeof(double),
+                              m, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(e, "copy C to host");
+    }
+    int hh_rc = CMM_OK;
+    if (count) {
+        hh_rc = run_hh(nullptr, nullptr, dC, p, m, p, 1, 1, CMM_MEDIAN, tau, dI, dJ, dV, cap, count,
+                       scratch, s);
+        if (hh_rc != CMM_OK && hh_rc != CMM_ERR_CAPACITY) return hh_rc;
+        const int64_t n = std::min(*count, cap);
+        if (n > 0) {
+            Span sp("d2h_hh", s, 0);
+            e = cudaMemcpyAsync(I, dI, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(J, dJ, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(V, dV, n * sizeof(double), cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) return cuda_fail(e, "copy heavy hitters to host");
+        }
+    }
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "multiply_host sync");
+    if (hh_rc == CMM_ERR_CAPACITY)
+        return fail(CMM_ERR_CAPACITY, "%lld heavy hitters, capacity %lld", (long long)*count,
+                    (long long)cap);
+    return CMM_OK;
+}
+
 int cmm_mean_pairs(const double *R, const cmm_hashes *hs, int64_t P, const int32_t *I,
                    const int32_t *J, double *out, void *stream) {
     g_err.clear();
@@ -417,8 +636,12 @@ int cmm_mean_pairs(const double *R, const cmm_hashes *hs, int64_t P, const int32
     if (!R || !I || !J || !out) return fail(CMM_ERR_ARG, "null pointer");
     HashParams hp;
     fill_params(hs, hp);
-    cudaError_t e = launch_mean_pairs(R, hp, hs->d, hs->log2b, P, I, J, out,
-                                      static_cast<cudaStream_t>(stream));
+    cudaError_t e;
+    {
+        Span sp("mean_pairs", static_cast<cudaStream_t>(stream));
+        e = launch_mean_pairs(R, hp, hs->d, hs->log2b, P, I, J, out,
+                              static_cast<cudaStream_t>(stream));
+    }
     if (e != cudaSuccess) return cuda_fail(e, "mean pairs");
     return CMM_OK;
 }
