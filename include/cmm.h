@@ -101,6 +101,27 @@ int cmm_sketch(const void *A, int64_t lda, int32_t transA, const void *B, int64_
                int32_t dtype, int64_t m, int64_t k, int64_t p, const cmm_hashes *hs,
                int32_t prec, double *R, void *ws, size_t ws_bytes, void *stream);
 
+/* Size of the static scratch array used by cmm_sketch_noalloc (64 MiB). */
+#define CMM_SKETCH_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+
+/* cmm_sketch for callers that cannot allocate device memory (the paper has no
+ * counterpart: its CPU code allocates freely).  Such callers include serving
+ * processes that reserve their whole device-memory budget at start-up, plugins
+ * whose host application owns every device allocation, and latency-critical
+ * paths that cannot take cudaMalloc's implicit synchronisation.  Same
+ * arguments and result as cmm_sketch, without `ws`: the scratch is a static
+ * device array of CMM_SKETCH_NOALLOC_SCRATCH_BYTES in the library, held by
+ * every GPU that loads the library until the process exits.  A problem whose
+ * cmm_sketch_workspace_bytes exceeds that size is rejected with CMM_ERR_RANGE
+ * before anything runs.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the array, so calls
+ * that overlap on the GPU race and must be serialised by the caller.  The
+ * function calls no cudaMalloc/cudaFree or other allocating routine. */
+int cmm_sketch_noalloc(const void *A, int64_t lda, int32_t transA, const void *B, int64_t ldb,
+                       int32_t dtype, int64_t m, int64_t k, int64_t p, const cmm_hashes *hs,
+                       int32_t prec, double *R, void *stream);
+
 /* Bytes of `ws` needed by cmm_extract / cmm_heavy_hitters / cmm_threshold. */
 size_t cmm_extract_workspace_bytes(int64_t m, int64_t p, int32_t d);
 

@@ -43,6 +43,9 @@ struct SketchPlan {
     int64_t ldat, ldbp;    // leading dimensions of the operands the sketch reads
 };
 
+// Record `msg` as the calling thread's cmm_last_error() text; returns `code`.
+int set_error(int code, const char *msg);
+
 // ---- launchers (sketch.cu / sketch_f64.cu / finish.cu) ----
 cudaError_t launch_prep_A(const void *A, int64_t lda, int transA, int dtype, int prec,
                           int64_t m, int64_t k, void *At, int64_t ldat, cudaStream_t s);

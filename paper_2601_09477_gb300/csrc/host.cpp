@@ -345,6 +345,8 @@ uint64_t splitmix64(uint64_t &state) {
 
 }  // namespace
 
+int cmm::set_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
 extern "C" {
 
 const char *cmm_last_error(void) { return g_err.c_str(); }
