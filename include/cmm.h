@@ -192,6 +192,33 @@ int cmm_multiply_host(const void *A, int64_t lda, int32_t transA, const void *B,
 int cmm_mean_pairs(const double *R, const cmm_hashes *hs, int64_t P, const int32_t *I,
                    const int32_t *J, double *out, void *stream);
 
+/* Bytes of `ws` needed by cmm_backward (0 on invalid sizes, or when m + p is
+ * too large for the per-CTA gradient row and column in shared memory). */
+size_t cmm_backward_workspace_bytes(int64_t m, int64_t k, int64_t p, int32_t d, int32_t log2b,
+                                    int32_t dtype, int32_t prec, int32_t transA);
+
+/* Adjoint of the mean estimator (cmm_mean_pairs) for the loss
+ *   L(A, B) = sum_q W[q] * Chat_mean[I[q]][J[q]].
+ * The estimator is bilinear in (A, B) (it is linear in C = A B through the
+ * bucketed sketch of Algorithm 1), so with
+ *   G_r[w] = (1/d) sum_{q : h1_r(I_q) XOR h2_r(J_q) = w} W_q s1_r(I_q) s2_r(J_q)
+ * the gradients are
+ *   dA[i][t] = s1_r(i) sum_r (G_r XOR-conv y_{r,t})[h1_r(i)],
+ *   dB[t][j] = s2_r(j) sum_r (G_r XOR-conv x_{r,t})[h2_r(j)],
+ * each XOR convolution computed as (1/b) H((H G_r) o (H y)) (Sec. 3.2).  The
+ * paper has no gradient; this is the chain rule through its Compress.
+ * A, B: device, FP32 or FP64 (dtype), layouts as in cmm_sketch.  I, J: device
+ * int32 (P pairs); W: device FP64.  dA (device, A's dtype and layout: m x k,
+ * or k x m when transA; leading dimension ldda) and dB (device, k x p, lddb)
+ * are overwritten.  prec: CMM_PREC_F64 or CMM_PREC_F32 (butterflies).
+ * Errors: CMM_ERR_ARG, CMM_ERR_RANGE (m + p too large), CMM_ERR_WORKSPACE,
+ * CMM_ERR_CUDA. */
+int cmm_backward(const void *A, int64_t lda, int32_t transA, const void *B, int64_t ldb,
+                 int32_t dtype, int64_t m, int64_t k, int64_t p, const cmm_hashes *hs,
+                 int32_t prec, int64_t P, const int32_t *I, const int32_t *J, const double *W,
+                 void *dA, int64_t ldda, void *dB, int64_t lddb, void *ws, size_t ws_bytes,
+                 void *stream);
+
 /* Launch tracing (the library's profiling hook).  While enabled, every
  * kernel launch the library makes is bracketed by CUDA events recorded on the
  * caller's stream.  cmm_trace_enable(1) clears earlier records and starts

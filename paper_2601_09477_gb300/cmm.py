@@ -77,6 +77,9 @@ def _load() -> ctypes.CDLL:
                                              P, i64, f64, i64, P, P, P,
                                              ctypes.POINTER(ctypes.c_int64), P, sz, P]),
         "cmm_mean_pairs": (ctypes.c_int, [P, H, i64, P, P, P, P]),
+        "cmm_backward_workspace_bytes": (sz, [i64, i64, i64, i32, i32, i32, i32, i32]),
+        "cmm_backward": (ctypes.c_int, [P, i64, i32, P, i64, i32, i64, i64, i64, H, i32, i64,
+                                        P, P, P, P, i64, P, i64, P, sz, P]),
         "cmm_trace_enable": (ctypes.c_int, [i32]),
         "cmm_trace_read": (ctypes.c_int, [i32, P, P, P, P]),
         "cmm_last_error": (ctypes.c_char_p, []),
@@ -307,6 +310,29 @@ def multiply_host(A: torch.Tensor, B: torch.Tensor, h: Hashes, prec: str = "f32"
         return C, None
     n = cnt.value
     return C, (hh_out[0][:n], hh_out[1][:n], hh_out[2][:n])
+
+
+def backward(A: torch.Tensor, B: torch.Tensor, h: Hashes, I: torch.Tensor, J: torch.Tensor,
+             W: torch.Tensor, prec: str = "f32", transA: bool = False, stream=None):
+    """(dL/dA, dL/dB) of L = sum_q W[q] * mean-estimate[I[q], J[q]] (cmm_backward)."""
+    m, k, p, dt = _operands(A, B, transA)
+    pr = _PREC[prec]
+    dev = A.device
+    I = I.to(device=dev, dtype=torch.int32).contiguous()
+    J = J.to(device=dev, dtype=torch.int32).contiguous()
+    W = W.to(device=dev, dtype=torch.float64).contiguous()
+    need = lib.cmm_backward_workspace_bytes(m, k, p, h.d, h.log2b, dt, pr, int(transA))
+    if need == 0:
+        raise CmmError(ERR_RANGE, "cmm_backward does not support these sizes / dtypes")
+    ws = _workspace(need, dev)
+    dA = torch.empty_like(A, memory_format=torch.contiguous_format)
+    dB = torch.empty_like(B, memory_format=torch.contiguous_format)
+    _check(lib.cmm_backward(A.data_ptr(), max(A.stride(0), 1), int(transA), B.data_ptr(),
+                            max(B.stride(0), 1), dt, m, k, p, h.ref, pr, I.numel(), I.data_ptr(),
+                            J.data_ptr(), W.data_ptr(), dA.data_ptr(), max(dA.stride(0), 1),
+                            dB.data_ptr(), max(dB.stride(0), 1), ws.data_ptr(), ws.numel(),
+                            _stream(stream)))
+    return dA, dB
 
 
 def mean_pairs(R: torch.Tensor, h: Hashes, I: torch.Tensor, J: torch.Tensor,

@@ -107,6 +107,27 @@ cudaError_t launch_prep_A(const void *A, int64_t lda, int transA, int dtype, int
     return prep_A_t<float>(A, lda, transA, dtype, m, k, (float *)At, ldat, s);
 }
 
+cudaError_t launch_convert_out(const void *src, int src_f64, int64_t rows, int64_t cols,
+                               int transpose, void *dst, int dst_dtype, int64_t ldd,
+                               cudaStream_t s) {
+    if (rows == 0 || cols == 0) return cudaSuccess;
+    const dim3 blk(32, 8);
+    const unsigned gt = grid_for(((rows + 31) / 32) * ((cols + 31) / 32), 1);
+    const unsigned gc = grid_for(rows * cols, 256 * 8);
+#define CMM_CONV(TI, TO)                                                                       \
+    if (transpose)                                                                             \
+        transpose_kernel<TI, TO><<<gt, blk, 0, s>>>((const TI *)src, cols, rows, cols, (TO *)dst, ldd); \
+    else                                                                                       \
+        convert_kernel<TI, TO><<<gc, 256, 0, s>>>((const TI *)src, cols, rows, cols, (TO *)dst, ldd);
+    if (src_f64 && dst_dtype == CMM_F64) { CMM_CONV(double, double) }
+    else if (src_f64 && dst_dtype == CMM_F32) { CMM_CONV(double, float) }
+    else if (!src_f64 && dst_dtype == CMM_F64) { CMM_CONV(float, double) }
+    else if (!src_f64 && dst_dtype == CMM_F32) { CMM_CONV(float, float) }
+    else return cudaErrorInvalidValue;
+#undef CMM_CONV
+    return cudaGetLastError();
+}
+
 cudaError_t launch_prep_B(const void *B, int64_t ldb, int dtype, int prec, int64_t k, int64_t p,
                           void *Bp, int64_t ldbp, cudaStream_t s) {
     if (prec == CMM_PREC_F64) return prep_B_t<double>(B, ldb, dtype, k, p, (double *)Bp, ldbp, s);
