@@ -219,6 +219,63 @@ int cmm_backward(const void *A, int64_t lda, int32_t transA, const void *B, int6
                  void *dA, int64_t ldda, void *dB, int64_t lddb, void *ws, size_t ws_bytes,
                  void *stream);
 
+/* ---- many independent problems in one persistent launch ------------------
+ * Each problem runs the whole path of Algorithm 1 (Compress and Decompress of
+ * every entry) with its own sizes, sketch length and hash functions; the
+ * repetition count d is shared.  The paper runs one problem at a time; this
+ * batched form is the library's own. */
+typedef struct {
+    const void *A;                 /* device, A^T stored k x m row-major (transA must be 1) */
+    int64_t lda;                   /* >= m */
+    int32_t transA;                /* must be 1: the left operand transposed (Sec. 4.3) */
+    const void *B;                 /* device, k x p row-major */
+    int64_t ldb;                   /* >= p */
+    int64_t m, k, p;
+    int32_t log2b;                 /* 5 .. CMM_MAX_LOG2B */
+    const uint64_t *hash_params;   /* host, 8*d words as in cmm_hashes.params */
+    double *R;                     /* device out, d x 2^log2b FP64 */
+    double *C;                     /* device out, m x p FP64 (NULL: sketch only) */
+    int64_t ldc;                   /* >= p when C is set */
+    int32_t tile_log2;             /* b-tile: log2 of the slice one CTA transforms, 0 = default */
+    int64_t t_tile;                /* t-tile: inner indices per sketch task, 0 = default */
+} cmm_problem;
+
+/* Host-side handle filled by cmm_batched_prepare (no device memory). */
+typedef struct {
+    uint64_t opaque[32];
+} cmm_batch_plan;
+
+/* Bytes of `ws` for a batch (0 on invalid problems).  Supported: dtype
+ * CMM_F32, prec CMM_PREC_F32. */
+size_t cmm_batched_workspace_bytes(const cmm_problem *problems, int32_t Q, int32_t d,
+                                   int32_t dtype, int32_t prec);
+
+/* Validate the Q problems (host array), lay out `ws` and upload the task
+ * table, problem descriptors and hash functions into it; synchronises
+ * `stream`.  The operand and output pointers are recorded: later launches read
+ * and write the same buffers.  Errors: CMM_ERR_ARG, CMM_ERR_RANGE,
+ * CMM_ERR_WORKSPACE, CMM_ERR_CUDA. */
+int cmm_batched_prepare(const cmm_problem *problems, int32_t Q, int32_t d, int32_t dtype,
+                        int32_t prec, void *ws, size_t ws_bytes, cmm_batch_plan *plan,
+                        void *stream);
+
+/* One run of every problem: a memset of the task counters and ONE persistent
+ * kernel launch on `stream`, both capturable in a CUDA graph.  Asynchronous. */
+int cmm_batched_launch(const cmm_batch_plan *plan, void *stream);
+
+/* cmm_batched_launch with explicit wait settings: `wait_budget_us` bounds
+ * every dependency wait inside the kernel (0 = the default of about 4 s), and
+ * a nonzero `unmet_dependency` raises each finish task's dependency target by
+ * one so that no wait can be met -- the kernel then gives up after the
+ * budget, sets its error word and returns, which lets a test exercise the
+ * CMM_ERR_TIMEOUT path without faulting or hanging the GPU. */
+int cmm_batched_launch_opts(const cmm_batch_plan *plan, int64_t wait_budget_us,
+                            int32_t unmet_dependency, void *stream);
+
+/* Synchronise `stream` and report whether the last launch finished:
+ * CMM_ERR_TIMEOUT when a bounded dependency wait inside the kernel ran out. */
+int cmm_batched_status(const cmm_batch_plan *plan, void *stream);
+
 /* Launch tracing (the library's profiling hook).  While enabled, every
  * kernel launch the library makes is bracketed by CUDA events recorded on the
  * caller's stream.  cmm_trace_enable(1) clears earlier records and starts

@@ -80,6 +80,11 @@ def _load() -> ctypes.CDLL:
         "cmm_backward_workspace_bytes": (sz, [i64, i64, i64, i32, i32, i32, i32, i32]),
         "cmm_backward": (ctypes.c_int, [P, i64, i32, P, i64, i32, i64, i64, i64, H, i32, i64,
                                         P, P, P, P, i64, P, i64, P, sz, P]),
+        "cmm_batched_workspace_bytes": (sz, [P, i32, i32, i32, i32]),
+        "cmm_batched_prepare": (ctypes.c_int, [P, i32, i32, i32, i32, P, sz, P, P]),
+        "cmm_batched_launch": (ctypes.c_int, [P, P]),
+        "cmm_batched_launch_opts": (ctypes.c_int, [P, i64, i32, P]),
+        "cmm_batched_status": (ctypes.c_int, [P, P]),
         "cmm_trace_enable": (ctypes.c_int, [i32]),
         "cmm_trace_read": (ctypes.c_int, [i32, P, P, P, P]),
         "cmm_last_error": (ctypes.c_char_p, []),
@@ -333,6 +338,75 @@ def backward(A: torch.Tensor, B: torch.Tensor, h: Hashes, I: torch.Tensor, J: to
                             dB.data_ptr(), max(dB.stride(0), 1), ws.data_ptr(), ws.numel(),
                             _stream(stream)))
     return dA, dB
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("transA", ctypes.c_int32),
+                ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64), ("m", ctypes.c_int64),
+                ("k", ctypes.c_int64), ("p", ctypes.c_int64), ("log2b", ctypes.c_int32),
+                ("hash_params", ctypes.POINTER(ctypes.c_uint64)), ("R", ctypes.c_void_p),
+                ("C", ctypes.c_void_p), ("ldc", ctypes.c_int64), ("tile_log2", ctypes.c_int32),
+                ("t_tile", ctypes.c_int64)]
+
+
+class _BatchPlan(ctypes.Structure):
+    _fields_ = [("opaque", ctypes.c_uint64 * 32)]
+
+
+@dataclass
+class Problem:
+    """One problem of a batch: At holds A^T (k x m, float32), B (k x p, float32)."""
+    At: torch.Tensor
+    B: torch.Tensor
+    hashes: Hashes
+    R: torch.Tensor | None = None
+    C: torch.Tensor | None = None
+    tile_log2: int = 0
+    t_tile: int = 0
+
+
+class Batch:
+    """A prepared batch: ``launch()`` runs every problem in one persistent
+    kernel launch (capturable in a CUDA graph), ``status()`` checks it."""
+
+    def __init__(self, problems, d: int, with_C: bool = True, ws: torch.Tensor | None = None,
+                 stream=None):
+        self.problems = list(problems)
+        self.d = d
+        arr = (_Problem * len(self.problems))()
+        for q, pb in enumerate(self.problems):
+            if pb.At.dtype != torch.float32 or pb.B.dtype != torch.float32:
+                raise TypeError("batched problems take float32 operands")
+            k, m = pb.At.shape
+            k2, p = pb.B.shape
+            if k != k2 or pb.hashes.d != d:
+                raise ValueError("problem %d: shape or hash count mismatch" % q)
+            if pb.R is None:
+                pb.R = torch.empty((d, pb.hashes.b), dtype=torch.float64, device=pb.At.device)
+            if with_C and pb.C is None:
+                pb.C = torch.empty((m, p), dtype=torch.float64, device=pb.At.device)
+            arr[q] = _Problem(pb.At.data_ptr(), max(pb.At.stride(0), 1), 1, pb.B.data_ptr(),
+                              max(pb.B.stride(0), 1), m, k, p, pb.hashes.log2b,
+                              pb.hashes.params.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                              pb.R.data_ptr(), pb.C.data_ptr() if pb.C is not None else None,
+                              pb.C.stride(0) if pb.C is not None else 0, int(pb.tile_log2),
+                              int(pb.t_tile))
+        self._arr = arr
+        need = lib.cmm_batched_workspace_bytes(arr, len(arr), d, F32, PREC_F32)
+        if need == 0:
+            raise CmmError(ERR_ARG, "invalid batch: " + lib.cmm_last_error().decode())
+        dev = self.problems[0].At.device
+        self.ws = ws if ws is not None and ws.numel() >= need else _workspace(need, dev)
+        self.plan = _BatchPlan()
+        _check(lib.cmm_batched_prepare(arr, len(arr), d, F32, PREC_F32, self.ws.data_ptr(),
+                                       self.ws.numel(), ctypes.byref(self.plan), _stream(stream)))
+
+    def launch(self, stream=None, wait_budget_us: int = 0, unmet_dependency: bool = False):
+        _check(lib.cmm_batched_launch_opts(ctypes.byref(self.plan), int(wait_budget_us),
+                                           int(bool(unmet_dependency)), _stream(stream)))
+
+    def status(self, stream=None) -> int:
+        return int(lib.cmm_batched_status(ctypes.byref(self.plan), _stream(stream)))
 
 
 def mean_pairs(R: torch.Tensor, h: Hashes, I: torch.Tensor, J: torch.Tensor,

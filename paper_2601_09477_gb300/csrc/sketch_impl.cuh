@@ -59,29 +59,23 @@ __device__ __forceinline__ void scatter_column(T *Sg, const T *__restrict__ col,
     }
 }
 
+// One CTA's work item: repetition r (hash functions H), frequency slice u_hi,
+// inner indices [t0, t1); writes its FP64 partial Z slice to `out` (N values).
+// smem_raw must hold sketch_smem_bytes<L, LE, THREADS, T>() bytes.
 template <typename T, typename TZ, int L, int LE, int THREADS>
-__global__ void __launch_bounds__(THREADS, (THREADS >= 512 ? 1 : 2))
-sketch_kernel(const T *__restrict__ At, int64_t ldat, const T *__restrict__ Bp, int64_t ldbp,
-              int64_t m, int64_t k, int64_t p, int Lfull, int C, int64_t chunk, int d,
-              const __grid_constant__ HashParams hp, double *__restrict__ partial) {
+__device__ __forceinline__ void sketch_block(const T *__restrict__ At, int64_t ldat,
+                                             const T *__restrict__ Bp, int64_t ldbp, int64_t m,
+                                             int64_t p, int Lfull, uint32_t u_hi, int64_t t0,
+                                             int64_t t1, const HashRep &H,
+                                             double *__restrict__ out, unsigned char *smem_raw) {
     using S = FwhtShape<L, LE>;
     constexpr int E = S::E, P = S::P, G = THREADS / P;
     static_assert(THREADS % P == 0, "CTA must hold whole groups");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
 
     const int tid = threadIdx.x;
     const int g = tid / P, q = tid % P;
     T *Sg = sm + g * S::STRIDE;
-
-    int item = blockIdx.x;
-    const uint32_t u_hi = (uint32_t)(item % C);
-    item /= C;
-    const int r = item % d;
-    const int64_t blk = item / d;
-    const int64_t t0 = blk * chunk;
-    const int64_t t1 = (t0 + chunk < k) ? t0 + chunk : k;
-    const HashRep H = hp.rep[r];
     const int shift = 64 - Lfull;
 
     for (int i = tid; i < G * S::STRIDE; i += THREADS) sm[i] = T(0);
@@ -113,8 +107,6 @@ sketch_kernel(const T *__restrict__ At, int64_t ldat, const T *__restrict__ Bp, 
         group_sync<P>(g);
     }
 
-    const int64_t b = (int64_t)1 << Lfull;
-    double *out = partial + ((int64_t)blk * d + r) * b + (int64_t)u_hi * S::N;
     if constexpr (G == 1) {
 #pragma unroll
         for (int j = 0; j < E; ++j) out[final_index<L, LE>(q, j)] = (double)z[j];
@@ -133,6 +125,25 @@ sketch_kernel(const T *__restrict__ At, int64_t ldat, const T *__restrict__ Bp, 
         }
         for (int i = tid; i < S::N; i += THREADS) out[i] = acc[i];
     }
+}
+
+template <typename T, typename TZ, int L, int LE, int THREADS>
+__global__ void __launch_bounds__(THREADS, (THREADS >= 512 ? 1 : 2))
+sketch_kernel(const T *__restrict__ At, int64_t ldat, const T *__restrict__ Bp, int64_t ldbp,
+              int64_t m, int64_t k, int64_t p, int Lfull, int C, int64_t chunk, int d,
+              const __grid_constant__ HashParams hp, double *__restrict__ partial) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int item = blockIdx.x;
+    const uint32_t u_hi = (uint32_t)(item % C);
+    item /= C;
+    const int r = item % d;
+    const int64_t blk = item / d;
+    const int64_t t0 = blk * chunk;
+    const int64_t t1 = (t0 + chunk < k) ? t0 + chunk : k;
+    const int64_t b = (int64_t)1 << Lfull;
+    double *out = partial + (blk * d + r) * b + (int64_t)u_hi * (1 << L);
+    sketch_block<T, TZ, L, LE, THREADS>(At, ldat, Bp, ldbp, m, p, Lfull, u_hi, t0, t1, hp.rep[r],
+                                        out, smem_raw);
 }
 
 // launch one instantiation; smem must be set up by the caller's attribute call

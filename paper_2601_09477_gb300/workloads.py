@@ -142,6 +142,36 @@ def batch_problems(count: int = 256, lo: int = 512, hi: int = 4096, spikes: int 
     return out
 
 
+def batch_problems_device(count: int = 256, lo: int = 512, hi: int = 4096, spikes: int = 16,
+                          log2b_lo: int = 10, log2b_hi: int = 15, seed: int = 1004,
+                          device="cuda", uniform_log2b: int | None = None):
+    """The distribution of ``batch_problems`` drawn on a torch device, with the
+    left operand produced directly transposed (A^T, k x m, float32).  Sizes,
+    sketch lengths and spike positions come from NumPy PCG64(seed); entries
+    from a torch generator seeded with ``seed``.  Returns a list of
+    (At, B, log2b, spike positions)."""
+    import torch
+    g = rng(seed)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    out = []
+    for _ in range(count):
+        m, k, p = (int(v) for v in g.integers(lo, hi + 1, size=3))
+        At = torch.randn(k, m, generator=gen, device=device, dtype=torch.float32)
+        B = torch.randn(k, p, generator=gen, device=device, dtype=torch.float32)
+        cnt = min(spikes, k)
+        ts = g.choice(k, size=cnt, replace=False)
+        ii = g.integers(0, m, size=cnt)
+        jj = g.integers(0, p, size=cnt)
+        a = math.sqrt(50.0 * math.sqrt(k))
+        for i, t, j in zip(ii, ts, jj):
+            At[int(t), int(i)] += a
+            B[int(t), int(j)] += a
+        L = uniform_log2b if uniform_log2b is not None else int(g.integers(log2b_lo, log2b_hi + 1))
+        out.append((At, B, L, np.stack([ii, jj], axis=1)))
+    return out
+
+
 def diff_problem(n: int = 4096, spikes: int = 256, pairs: int = 4096, seed: int = 1005,
                  dtype=np.float32, spike_value: float = 1.0):
     """(A, B, I, J, W): N(0,1)/sqrt(n) operands with planted spikes, and a fixed
