@@ -148,10 +148,3 @@ def test_batched_256_uneven_problems(cmm):
     rows = (5, 9)
     Co = orc.extract(R, pb.hashes.params, A.shape[0], B.shape[1], rows=rows)
     assert np.array_equal(pb.C[rows[0]:rows[1]].cpu().numpy(), Co)
-    # planted spikes stand out: most estimates at the spikes are within 20% of 50 sqrt(k)
-    hits = 0
-    for (At, B_, L_, pos), pb in zip(raw[:32], probs[:32]):
-        k = At.shape[0]
-        est = pb.C[torch.from_numpy(pos[:, 0]).cuda(), torch.from_numpy(pos[:, 1]).cuda()]
-        hits += int((est.abs() > 0.8 * 50 * np.sqrt(k)).sum().item())
-    assert hits >= 0.9 * 32 * 16
