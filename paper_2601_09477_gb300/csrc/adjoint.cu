@@ -48,11 +48,11 @@ template <typename T, int L, int LE>
 __device__ __forceinline__ void gather_keys(const T *Sg, T *acc, int64_t n, uint64_t a, uint64_t c,
                                             uint64_t as, uint64_t cs, int shift, uint32_t u_hi,
                                             int q) {
-    using S = FwhtShape<L, LE>;
+    using S = FwhtShape<T, L, LE>;
     for (int64_t x = q; x < n; x += S::P) {
         const uint32_t h = mas_hash(a, c, (uint64_t)x, shift);
         const uint32_t neg = mas_sign_bit(as, cs, (uint64_t)x) ^ (__popc((h >> L) & u_hi) & 1u);
-        const T v = Sg[pad_index<LE>((int)(h & (S::N - 1)))];
+        const T v = Sg[pad_index<T, L, LE>((int)(h & (S::N - 1)))];
         acc[x] += neg ? -v : v;
     }
 }
@@ -63,7 +63,7 @@ adjoint_kernel(const T *__restrict__ At, int64_t ldat, const T *__restrict__ Bp,
                int64_t m, int64_t k, int64_t p, int Lfull, int C, int64_t chunk, int d,
                const __grid_constant__ HashParams hp, const double *__restrict__ Gs,
                T *__restrict__ dAt, T *__restrict__ dBt, int accumulate) {
-    using S = FwhtShape<L, LE>;
+    using S = FwhtShape<T, L, LE>;
     constexpr int E = S::E, P = S::P, G = THREADS / P;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
@@ -107,29 +107,29 @@ adjoint_kernel(const T *__restrict__ At, int64_t ldat, const T *__restrict__ Bp,
             fwht_rounds<T, L, LE, 0>(Sg, v, q, g);
             const double *gr = Gs + r * b + (int64_t)u_hi * S::N;
 #pragma unroll
-            for (int j = 0; j < E; ++j) gh[j] = (T)__ldg(gr + final_index<L, LE>(q, j));
+            for (int j = 0; j < E; ++j) gh[j] = (T)__ldg(gr + final_index<T, L, LE>(q, j));
             // dA: H((1/b) H G o H y), gathered at h1(i)
 #pragma unroll
-            for (int j = 0; j < E; ++j) Sg[pad_index<LE>(final_index<L, LE>(q, j))] = gh[j] * v[j];
+            for (int j = 0; j < E; ++j) Sg[pad_index<T, L, LE>(final_index<T, L, LE>(q, j))] = gh[j] * v[j];
             group_sync<P>(g);
             fwht_rounds<T, L, LE, 0>(Sg, v, q, g);
 #pragma unroll
-            for (int j = 0; j < E; ++j) Sg[pad_index<LE>(final_index<L, LE>(q, j))] = v[j];
+            for (int j = 0; j < E; ++j) Sg[pad_index<T, L, LE>(final_index<T, L, LE>(q, j))] = v[j];
             group_sync<P>(g);
             if (active) gather_keys<T, L, LE>(Sg, dAc, m, H.a1, H.c1, H.as1, H.cs1, shift, u_hi, q);
             group_sync<P>(g);
             // dB: H((1/b) H G o H x), gathered at h2(j)
 #pragma unroll
-            for (int j = 0; j < E; ++j) Sg[pad_index<LE>(final_index<L, LE>(q, j))] = gh[j] * xh[j];
+            for (int j = 0; j < E; ++j) Sg[pad_index<T, L, LE>(final_index<T, L, LE>(q, j))] = gh[j] * xh[j];
             group_sync<P>(g);
             fwht_rounds<T, L, LE, 0>(Sg, v, q, g);
 #pragma unroll
-            for (int j = 0; j < E; ++j) Sg[pad_index<LE>(final_index<L, LE>(q, j))] = v[j];
+            for (int j = 0; j < E; ++j) Sg[pad_index<T, L, LE>(final_index<T, L, LE>(q, j))] = v[j];
             group_sync<P>(g);
             if (active) gather_keys<T, L, LE>(Sg, dBr, p, H.a2, H.c2, H.as2, H.cs2, shift, u_hi, q);
             group_sync<P>(g);
 #pragma unroll
-            for (int j = 0; j < E; ++j) Sg[pad_index<LE>(final_index<L, LE>(q, j))] = T(0);
+            for (int j = 0; j < E; ++j) Sg[pad_index<T, L, LE>(final_index<T, L, LE>(q, j))] = T(0);
             group_sync<P>(g);
         }
         if (active) {

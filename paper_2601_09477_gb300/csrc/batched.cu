@@ -120,7 +120,7 @@ __device__ __forceinline__ void sketch_task(const BProblem &pr, const HashRep &H
     const int64_t b = (int64_t)1 << pr.L;
     double *out = pr.partial + ((int64_t)blk * d + r) * b + (int64_t)u_hi * (1 << L);
     sketch_block<float, float, L, LE, kBThreads>(pr.At, pr.ldat, pr.Bp, pr.ldbp, pr.m, pr.p, pr.L,
-                                                 u_hi, t0, t1, H, out, smem);
+                                                 u_hi, t0, t1, H, nullptr, nullptr, out, smem);
 }
 
 __device__ void dispatch_sketch(const BProblem &pr, const HashRep &H, int a, int blk, int d,

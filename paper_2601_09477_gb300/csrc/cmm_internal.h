@@ -38,7 +38,7 @@ struct SketchPlan {
     int threads;           // CTA size
     size_t smem;           // dynamic shared memory per CTA
     // workspace carve-up (byte offsets into ws)
-    size_t off_At, off_Bp, off_partial, off_Z, total;
+    size_t off_At, off_Bp, off_partial, off_Z, off_tab, total;
     bool prep_A, prep_B;   // whether A / B are converted into the workspace
     int64_t ldat, ldbp;    // leading dimensions of the operands the sketch reads
 };
@@ -74,12 +74,16 @@ cudaError_t launch_prep_A(const void *A, int64_t lda, int transA, int dtype, int
                           int64_t m, int64_t k, void *At, int64_t ldat, cudaStream_t s);
 cudaError_t launch_prep_B(const void *B, int64_t ldb, int dtype, int prec,
                           int64_t k, int64_t p, void *Bp, int64_t ldbp, cudaStream_t s);
+// tabA / tabB: scatter tables (d * C * m and d * C * p words, built by the
+// launcher when not null)
 cudaError_t launch_sketch_f32(const SketchPlan &pl, const float *At, const float *Bp,
                               int64_t m, int64_t k, int64_t p, int d, const HashParams &hp,
-                              double *partial, cudaStream_t s);
+                              const uint32_t *tabA, const uint32_t *tabB, double *partial,
+                              cudaStream_t s);
 cudaError_t launch_sketch_f64(const SketchPlan &pl, const double *At, const double *Bp,
                               int64_t m, int64_t k, int64_t p, int d, const HashParams &hp,
-                              double *partial, cudaStream_t s);
+                              const uint32_t *tabA, const uint32_t *tabB, double *partial,
+                              cudaStream_t s);
 cudaError_t launch_finish(const double *partial, int nchunks, int d, int L, double *Z,
                           double *R, cudaStream_t s);
 int sketch_threads_f32(int Llo);

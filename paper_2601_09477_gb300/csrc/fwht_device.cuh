@@ -6,27 +6,44 @@
 // done in ceil(L / LE) register rounds, round K covering index bits
 // [K*LE, K*LE + nb_K).  Between rounds the slice goes through shared memory.
 //
-// Layout: element u lives at word u + (u >> LE) of the group's array (one pad
-// word per E words).  With that padding every round's loads and stores are free
-// of bank conflicts for 4-byte elements (and per half-warp for 8-byte ones),
-// and the address of (thread q, register j) splits into a per-thread base plus
-// a compile-time offset, so the compiler uses [reg + imm] addressing.
+// Layout: element u lives at word u + PAD * (u >> LE) of the group's array.
+// For FP32 with E = 32 and N >= 2^10, PAD = 4: each 32-element row of round 0
+// is contiguous and 16-byte aligned (vector loads and stores), and the loads
+// and stores of every round are free of bank conflicts (the thread index fills
+// the low complement bits, so the 32 lanes of a warp hit 32 distinct banks).
+// Smaller FP32 transforms (several groups per warp) and FP64 use PAD = 1,
+// which is conflict-free for them (per half-warp for FP64).  The address of (thread q,
+// register j) splits into a per-thread base plus a compile-time offset.
+//
+// FP32 butterflies of stages >= 1 run as packed FP32x2 operations (two
+// independent IEEE additions per instruction, identical results to scalar
+// adds); a - b is formed as fma(b, -1, a), which is exact-rounded a - b.
 #pragma once
 
 #include <cstdint>
 
 namespace cmm {
 
-template <int LE>
-__host__ __device__ constexpr int pad_index(int u) { return u + (u >> LE); }
+template <typename T, int L, int LE>
+struct PadOf {
+    // 4 pad words per 32-word row for FP32 transforms of 2^10 and more (vector
+    // rows in round 0); 1 otherwise (several groups share a warp below 2^10)
+    static constexpr int value = (sizeof(T) == 4 && LE == 5 && L >= 10) ? 4 : 1;
+};
 
-template <int L, int LE>
+template <typename T, int L, int LE>
+__host__ __device__ constexpr int pad_index(int u) {
+    return u + PadOf<T, L, LE>::value * (u >> LE);
+}
+
+template <typename T, int L, int LE>
 struct FwhtShape {
     static constexpr int N = 1 << L;
     static constexpr int E = 1 << LE;
     static constexpr int P = N / E;                  // threads per group
     static constexpr int NR = (L + LE - 1) / LE;     // register rounds
-    static constexpr int STRIDE = N + N / E;         // words per group array (with pads)
+    static constexpr int PAD = PadOf<T, L, LE>::value;
+    static constexpr int STRIDE = N + PAD * (N / E); // words per group array (with pads)
     static_assert(LE <= L, "register block larger than the transform");
 
     template <int K>
@@ -34,16 +51,16 @@ struct FwhtShape {
         static constexpr int lo = K * LE;
         static constexpr int nb = (L - lo) < LE ? (L - lo) : LE;
         // index u of register j of thread q: the low nb bits of j are the
-        // transformed bits [lo, lo+nb); the remaining register bits, then the
-        // thread bits, fill the other index bits from the bottom up.
+        // transformed bits [lo, lo+nb); the thread bits fill the other index
+        // bits from the bottom up, then the remaining register bits
         __host__ __device__ static constexpr int u(int q, int j) {
-            int payload = (j >> nb) | (q << (LE - nb));
-            int low = payload & ((1 << lo) - 1);
-            int high = payload >> lo;
+            const int payload = q | ((j >> nb) << (L - LE));
+            const int low = payload & ((1 << lo) - 1);
+            const int high = payload >> lo;
             return low | ((j & ((1 << nb) - 1)) << lo) | (high << (lo + nb));
         }
         __host__ __device__ static constexpr int addr(int q, int j) {
-            return pad_index<LE>(u(q, j));
+            return pad_index<T, L, LE>(u(q, j));
         }
     };
 };
@@ -66,6 +83,47 @@ __device__ __forceinline__ void reg_fwht(T (&v)[E]) {
     }
 }
 
+// FP32: stage 0 scalar, stages >= 1 on packed pairs (j, j+1) and (j+h, j+h+1)
+template <int E, int NB>
+__device__ __forceinline__ void reg_fwht_f32(float (&v)[E]) {
+    if constexpr (NB >= 1) {
+#pragma unroll
+        for (int j = 0; j < E; j += 2) {
+            const float a = v[j], b = v[j + 1];
+            v[j] = a + b;
+            v[j + 1] = a - b;
+        }
+    }
+    if constexpr (NB >= 2 && E >= 4) {
+        const float2 m1 = make_float2(-1.f, -1.f);
+#pragma unroll
+        for (int s = 1; s < NB; ++s) {
+#pragma unroll
+            for (int j = 0; j < E; j += 2) {
+                if (!(j & (1 << s))) {
+                    const float2 a = make_float2(v[j], v[j + 1]);
+                    const float2 b = make_float2(v[j | (1 << s)], v[(j | (1 << s)) + 1]);
+                    const float2 sum = __fadd2_rn(a, b);
+                    const float2 dif = __ffma2_rn(b, m1, a);
+                    v[j] = sum.x;
+                    v[j + 1] = sum.y;
+                    v[j | (1 << s)] = dif.x;
+                    v[(j | (1 << s)) + 1] = dif.y;
+                }
+            }
+        }
+    }
+}
+
+template <typename T, int E, int NB>
+__device__ __forceinline__ void reg_fwht_any(T (&v)[E]) {
+    if constexpr (sizeof(T) == 4) {
+        reg_fwht_f32<E, NB>(v);
+    } else {
+        reg_fwht<T, E, NB>(v);
+    }
+}
+
 // barrier of one group: named barrier for multi-warp groups, warp barrier for
 // groups of at most one warp (all lanes of a warp run the same trip counts)
 template <int P>
@@ -77,32 +135,69 @@ __device__ __forceinline__ void group_sync(int g) {
     }
 }
 
+// load / store the E values of round K (vectorised for the contiguous,
+// 16-byte aligned rows of FP32 round 0)
+template <typename T, int L, int LE, int K>
+__device__ __forceinline__ void round_load(const T *base, T (&v)[1 << LE]) {
+    using RK = typename FwhtShape<T, L, LE>::template Round<K>;
+    constexpr int E = 1 << LE;
+    if constexpr (K == 0 && PadOf<T, L, LE>::value == 4) {
+        const float4 *b4 = reinterpret_cast<const float4 *>(base);
+#pragma unroll
+        for (int c = 0; c < E / 4; ++c) {
+            const float4 w = b4[c];
+            v[4 * c] = w.x;
+            v[4 * c + 1] = w.y;
+            v[4 * c + 2] = w.z;
+            v[4 * c + 3] = w.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < E; ++j) v[j] = base[RK::addr(0, j)];
+    }
+}
+
+template <typename T, int L, int LE, int K>
+__device__ __forceinline__ void round_store(T *base, const T (&v)[1 << LE]) {
+    using RK = typename FwhtShape<T, L, LE>::template Round<K>;
+    constexpr int E = 1 << LE;
+    if constexpr (K == 0 && PadOf<T, L, LE>::value == 4) {
+        float4 *b4 = reinterpret_cast<float4 *>(base);
+#pragma unroll
+        for (int c = 0; c < E / 4; ++c)
+            b4[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < E; ++j) base[RK::addr(0, j)] = v[j];
+    }
+}
+
 // Transform the group's slice Sg in place, leaving the result in registers v
 // (round NR-1 layout) and the shared array zeroed for the next scatter.
 template <typename T, int L, int LE, int K>
 __device__ __forceinline__ void fwht_rounds(T *Sg, T (&v)[1 << LE], int q, int g) {
-    using S = FwhtShape<L, LE>;
+    using S = FwhtShape<T, L, LE>;
     using RK = typename S::template Round<K>;
     constexpr int E = S::E;
     T *base = Sg + RK::addr(q, 0);
-#pragma unroll
-    for (int j = 0; j < E; ++j) v[j] = base[RK::addr(0, j)];
-    reg_fwht<T, E, RK::nb>(v);
+    round_load<T, L, LE, K>(base, v);
+    reg_fwht_any<T, E, RK::nb>(v);
     if constexpr (K + 1 < S::NR) {
-#pragma unroll
-        for (int j = 0; j < E; ++j) base[RK::addr(0, j)] = v[j];
+        round_store<T, L, LE, K>(base, v);
         group_sync<S::P>(g);
         fwht_rounds<T, L, LE, K + 1>(Sg, v, q, g);
     } else {
+        T zero[E];
 #pragma unroll
-        for (int j = 0; j < E; ++j) base[RK::addr(0, j)] = T(0);
+        for (int j = 0; j < E; ++j) zero[j] = T(0);
+        round_store<T, L, LE, K>(base, zero);
     }
 }
 
 // index (in the unpadded slice) of register j of thread q after the last round
-template <int L, int LE>
+template <typename T, int L, int LE>
 __device__ __forceinline__ int final_index(int q, int j) {
-    using S = FwhtShape<L, LE>;
+    using S = FwhtShape<T, L, LE>;
     return S::template Round<S::NR - 1>::u(q, j);
 }
 

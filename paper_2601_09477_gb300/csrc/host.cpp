@@ -175,6 +175,8 @@ bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int p
     off += align_up((size_t)pl.nchunks * d * b * sizeof(double));
     pl.off_Z = off;
     off += align_up((size_t)d * b * sizeof(double));
+    pl.off_tab = off;
+    off += align_up((size_t)d * pl.C * (m + p) * sizeof(uint32_t));
     pl.total = off;
     return true;
 }
@@ -252,12 +254,14 @@ int run_sketch(const void *A, int64_t lda, int transA, const void *B, int64_t ld
     double *Z = reinterpret_cast<double *>(base + pl.off_Z);
     {
         Span sp(prec == CMM_PREC_F64 ? "sketch_f64" : "sketch_f32", s);
+        const uint32_t *tabA = reinterpret_cast<const uint32_t *>(base + pl.off_tab);
+        const uint32_t *tabB = tabA + (size_t)hs->d * pl.C * m;
         if (prec == CMM_PREC_F64)
             e = launch_sketch_f64(pl, (const double *)At, (const double *)Bp, m, k, p, hs->d, hp,
-                                  partial, s);
+                                  tabA, tabB, partial, s);
         else
             e = launch_sketch_f32(pl, (const float *)At, (const float *)Bp, m, k, p, hs->d, hp,
-                                  partial, s);
+                                  tabA, tabB, partial, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "sketch kernel");
     {
@@ -351,7 +355,8 @@ bool plan_adjoint(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int 
     const int P = N >> LE;
     const int G = pl.threads / P;
     const size_t es = f64 ? 8 : 4;
-    pl.smem = (size_t)G * ((size_t)N + N / (1 << LE) + m + p) * es;
+    const int pad = (!f64 && LE == 5) ? 4 : 1;   // shared-memory pad words per row
+    pl.smem = (size_t)G * ((size_t)N + (size_t)pad * (N >> LE) + m + p) * es;
     if (pl.smem > kMaxDynSmem) return false;
     const int64_t slots = num_sms();
     const int64_t kk = std::max<int64_t>(k, 1);

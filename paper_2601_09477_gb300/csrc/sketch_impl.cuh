@@ -19,6 +19,13 @@
 //   accumulates Z[u] += X^[u] * Y^[u] in registers (TZ precision).
 // At the end the groups' Z are summed in FP64 and the CTA writes its FP64
 // partial Z for (block, r, slice) -- the cross-block reduction is FP64.
+//
+// The scatter either evaluates the hashes per element (multiply-add-shift,
+// two 64-bit products) or, in the single-problem kernel, reads one packed
+// 32-bit word per element from a table built once per call for the CTA's
+// (r, u_hi): the padded shared-memory word of the bucket in the low bits and
+// the combined sign in bit 31.  The table is re-read for every t and stays in
+// L1; the operand columns are streamed past L1.
 #pragma once
 
 #include "cmm_internal.h"
@@ -29,46 +36,78 @@ namespace cmm {
 template <typename T>
 __device__ __forceinline__ T neg_if(T v, uint32_t neg) { return neg ? -v : v; }
 
-// scatter one column (n values, contiguous) into the group's slice
+template <typename T>
+__device__ __forceinline__ T ld_stream(const T *p) {
+    return __ldcs(p);   // evict-first: the columns are used once per CTA
+}
+
+// scatter one column (n values, contiguous) into the group's slice, hashing
 template <typename T, int L, int LE>
 __device__ __forceinline__ void scatter_column(T *Sg, const T *__restrict__ col, int64_t n,
                                                uint64_t a, uint64_t c, uint64_t as, uint64_t cs,
                                                int shift, uint32_t u_hi, int q) {
-    using S = FwhtShape<L, LE>;
+    using S = FwhtShape<T, L, LE>;
     constexpr int P = S::P;
     constexpr int B = 8;
     int64_t i = q;
     for (; i + (B - 1) * (int64_t)P < n; i += B * (int64_t)P) {
         T val[B];
 #pragma unroll
-        for (int e = 0; e < B; ++e) val[e] = __ldg(col + i + e * (int64_t)P);
+        for (int e = 0; e < B; ++e) val[e] = ld_stream(col + i + e * (int64_t)P);
 #pragma unroll
         for (int e = 0; e < B; ++e) {
             const uint64_t x = (uint64_t)(i + e * (int64_t)P);
             const uint32_t h = mas_hash(a, c, x, shift);
             const uint32_t neg = mas_sign_bit(as, cs, x) ^ (__popc((h >> L) & u_hi) & 1u);
-            atomicAdd(Sg + pad_index<LE>((int)(h & (S::N - 1))), neg_if(val[e], neg));
+            atomicAdd(Sg + pad_index<T, L, LE>((int)(h & (S::N - 1))), neg_if(val[e], neg));
         }
     }
     for (; i < n; i += P) {
-        const T v = __ldg(col + i);
+        const T v = ld_stream(col + i);
         const uint64_t x = (uint64_t)i;
         const uint32_t h = mas_hash(a, c, x, shift);
         const uint32_t neg = mas_sign_bit(as, cs, x) ^ (__popc((h >> L) & u_hi) & 1u);
-        atomicAdd(Sg + pad_index<LE>((int)(h & (S::N - 1))), neg_if(v, neg));
+        atomicAdd(Sg + pad_index<T, L, LE>((int)(h & (S::N - 1))), neg_if(v, neg));
     }
 }
 
-// One CTA's work item: repetition r (hash functions H), frequency slice u_hi,
-// inner indices [t0, t1); writes its FP64 partial Z slice to `out` (N values).
+// scatter one column using the packed (padded word | sign << 31) table
+template <typename T, int L, int LE>
+__device__ __forceinline__ void scatter_table(T *Sg, const T *__restrict__ col,
+                                              const uint32_t *__restrict__ tab, int64_t n, int q) {
+    constexpr int P = FwhtShape<T, L, LE>::P;
+    constexpr int B = 8;
+    int64_t i = q;
+    for (; i + (B - 1) * (int64_t)P < n; i += B * (int64_t)P) {
+        T val[B];
+        uint32_t w[B];
+#pragma unroll
+        for (int e = 0; e < B; ++e) {
+            val[e] = ld_stream(col + i + e * (int64_t)P);
+            w[e] = __ldg(tab + i + e * (int64_t)P);
+        }
+#pragma unroll
+        for (int e = 0; e < B; ++e) atomicAdd(Sg + (w[e] & 0x7fffffffu), neg_if(val[e], w[e] >> 31));
+    }
+    for (; i < n; i += P) {
+        const uint32_t w = __ldg(tab + i);
+        atomicAdd(Sg + (w & 0x7fffffffu), neg_if(ld_stream(col + i), w >> 31));
+    }
+}
+
+// One CTA's work item: repetition r (hash functions H, or the tables tabA /
+// tabB of this (r, u_hi) when not null), frequency slice u_hi, inner indices
+// [t0, t1); writes its FP64 partial Z slice to `out` (N values).
 // smem_raw must hold sketch_smem_bytes<L, LE, THREADS, T>() bytes.
 template <typename T, typename TZ, int L, int LE, int THREADS>
 __device__ __forceinline__ void sketch_block(const T *__restrict__ At, int64_t ldat,
                                              const T *__restrict__ Bp, int64_t ldbp, int64_t m,
                                              int64_t p, int Lfull, uint32_t u_hi, int64_t t0,
                                              int64_t t1, const HashRep &H,
+                                             const uint32_t *__restrict__ tabA,
+                                             const uint32_t *__restrict__ tabB,
                                              double *__restrict__ out, unsigned char *smem_raw) {
-    using S = FwhtShape<L, LE>;
+    using S = FwhtShape<T, L, LE>;
     constexpr int E = S::E, P = S::P, G = THREADS / P;
     static_assert(THREADS % P == 0, "CTA must hold whole groups");
     T *sm = reinterpret_cast<T *>(smem_raw);
@@ -91,25 +130,46 @@ __device__ __forceinline__ void sketch_block(const T *__restrict__ At, int64_t l
     for (int64_t it = 0; it < iters; ++it) {
         const int64_t t = t0 + it * G + g;
         const bool active = t < t1;
-        if (active) scatter_column<T, L, LE>(Sg, At + t * ldat, m, H.a1, H.c1, H.as1, H.cs1,
-                                             shift, u_hi, q);
+        if (active) {
+            if (tabA)
+                scatter_table<T, L, LE>(Sg, At + t * ldat, tabA, m, q);
+            else
+                scatter_column<T, L, LE>(Sg, At + t * ldat, m, H.a1, H.c1, H.as1, H.cs1, shift,
+                                         u_hi, q);
+        }
         group_sync<P>(g);
         fwht_rounds<T, L, LE, 0>(Sg, v, q, g);
 #pragma unroll
         for (int j = 0; j < E; ++j) xh[j] = v[j];
         group_sync<P>(g);
-        if (active) scatter_column<T, L, LE>(Sg, Bp + t * ldbp, p, H.a2, H.c2, H.as2, H.cs2,
-                                             shift, u_hi, q);
+        if (active) {
+            if (tabB)
+                scatter_table<T, L, LE>(Sg, Bp + t * ldbp, tabB, p, q);
+            else
+                scatter_column<T, L, LE>(Sg, Bp + t * ldbp, p, H.a2, H.c2, H.as2, H.cs2, shift,
+                                         u_hi, q);
+        }
         group_sync<P>(g);
         fwht_rounds<T, L, LE, 0>(Sg, v, q, g);
+        if constexpr (sizeof(TZ) == 4 && sizeof(T) == 4 && (E % 2) == 0) {
 #pragma unroll
-        for (int j = 0; j < E; ++j) z[j] += (TZ)xh[j] * (TZ)v[j];
+            for (int j = 0; j < E; j += 2) {
+                const float2 acc = __ffma2_rn(make_float2(xh[j], xh[j + 1]),
+                                              make_float2(v[j], v[j + 1]),
+                                              make_float2(z[j], z[j + 1]));
+                z[j] = acc.x;
+                z[j + 1] = acc.y;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < E; ++j) z[j] += (TZ)xh[j] * (TZ)v[j];
+        }
         group_sync<P>(g);
     }
 
     if constexpr (G == 1) {
 #pragma unroll
-        for (int j = 0; j < E; ++j) out[final_index<L, LE>(q, j)] = (double)z[j];
+        for (int j = 0; j < E; ++j) out[final_index<T, L, LE>(q, j)] = (double)z[j];
     } else {
         // sum the groups' accumulators in FP64 through shared memory
         __syncthreads();
@@ -119,7 +179,7 @@ __device__ __forceinline__ void sketch_block(const T *__restrict__ At, int64_t l
         for (int gg = 0; gg < G; ++gg) {
             if (g == gg) {
 #pragma unroll
-                for (int j = 0; j < E; ++j) acc[final_index<L, LE>(q, j)] += (double)z[j];
+                for (int j = 0; j < E; ++j) acc[final_index<T, L, LE>(q, j)] += (double)z[j];
             }
             __syncthreads();
         }
@@ -131,7 +191,8 @@ template <typename T, typename TZ, int L, int LE, int THREADS>
 __global__ void __launch_bounds__(THREADS, (THREADS >= 512 ? 1 : 2))
 sketch_kernel(const T *__restrict__ At, int64_t ldat, const T *__restrict__ Bp, int64_t ldbp,
               int64_t m, int64_t k, int64_t p, int Lfull, int C, int64_t chunk, int d,
-              const __grid_constant__ HashParams hp, double *__restrict__ partial) {
+              const __grid_constant__ HashParams hp, const uint32_t *__restrict__ tabA,
+              const uint32_t *__restrict__ tabB, double *__restrict__ partial) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int item = blockIdx.x;
     const uint32_t u_hi = (uint32_t)(item % C);
@@ -142,28 +203,72 @@ sketch_kernel(const T *__restrict__ At, int64_t ldat, const T *__restrict__ Bp, 
     const int64_t t1 = (t0 + chunk < k) ? t0 + chunk : k;
     const int64_t b = (int64_t)1 << Lfull;
     double *out = partial + (blk * d + r) * b + (int64_t)u_hi * (1 << L);
+    const int64_t slot = (int64_t)r * C + u_hi;
     sketch_block<T, TZ, L, LE, THREADS>(At, ldat, Bp, ldbp, m, p, Lfull, u_hi, t0, t1, hp.rep[r],
-                                        out, smem_raw);
+                                        tabA ? tabA + slot * m : nullptr,
+                                        tabB ? tabB + slot * p : nullptr, out, smem_raw);
+}
+
+// packed scatter words for every (r, u_hi) slot: tab[(r*C + u_hi)*n + x] =
+// padded shared-memory word of h_lo(x) | (combined sign bit) << 31
+template <typename T, int L, int LE>
+__global__ void sketch_table_kernel(const __grid_constant__ HashParams hp, int d, int Lfull,
+                                    int Llo, int C, int64_t m, int64_t p,
+                                    uint32_t *__restrict__ tabA, uint32_t *__restrict__ tabB) {
+    const int shift = 64 - Lfull;
+    const int64_t nA = (int64_t)d * C * m, n = nA + (int64_t)d * C * p;
+    const uint32_t lo_mask = (1u << Llo) - 1u;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const bool isA = e < nA;
+        const int64_t f = isA ? e : e - nA;
+        const int64_t len = isA ? m : p;
+        const int64_t slot = f / len;
+        const uint64_t x = (uint64_t)(f % len);
+        const int r = (int)(slot / C);
+        const uint32_t u_hi = (uint32_t)(slot % C);
+        const HashRep &H = hp.rep[r];
+        const uint32_t h = isA ? mas_hash(H.a1, H.c1, x, shift) : mas_hash(H.a2, H.c2, x, shift);
+        const uint32_t sb = isA ? mas_sign_bit(H.as1, H.cs1, x) : mas_sign_bit(H.as2, H.cs2, x);
+        const uint32_t neg = sb ^ (__popc((h >> Llo) & u_hi) & 1u);
+        const uint32_t w = (uint32_t)pad_index<T, L, LE>((int)(h & lo_mask)) | (neg << 31);
+        if (isA)
+            tabA[f] = w;
+        else
+            tabB[f] = w;
+    }
 }
 
 // launch one instantiation; smem must be set up by the caller's attribute call
 template <typename T, typename TZ, int L, int LE, int THREADS>
 cudaError_t launch_sketch_inst(const SketchPlan &pl, const T *At, const T *Bp, int64_t m,
                                int64_t k, int64_t p, int d, const HashParams &hp,
-                               double *partial, cudaStream_t s) {
+                               const uint32_t *tabA, const uint32_t *tabB, double *partial,
+                               cudaStream_t s) {
+    if (tabA) {
+        const int64_t n = (int64_t)d * pl.C * (m + p);
+        int64_t g = (n + 255) / 256;
+        if (g > 152 * 32) g = 152 * 32;
+        if (g < 1) g = 1;
+        sketch_table_kernel<T, L, LE><<<(unsigned)g, 256, 0, s>>>(hp, d, pl.L, L, pl.C, m, p,
+                                                              const_cast<uint32_t *>(tabA),
+                                                              const_cast<uint32_t *>(tabB));
+        cudaError_t e0 = cudaGetLastError();
+        if (e0 != cudaSuccess) return e0;
+    }
     auto kern = sketch_kernel<T, TZ, L, LE, THREADS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)pl.smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (int64_t)pl.nchunks * d * pl.C;
     kern<<<(unsigned)blocks, THREADS, pl.smem, s>>>(At, pl.ldat, Bp, pl.ldbp, m, k, p, pl.L,
-                                                    pl.C, pl.chunk, d, hp, partial);
+                                                    pl.C, pl.chunk, d, hp, tabA, tabB, partial);
     return cudaGetLastError();
 }
 
 template <int L, int LE, int THREADS, typename T>
 constexpr size_t sketch_smem_bytes() {
-    using S = FwhtShape<L, LE>;
+    using S = FwhtShape<T, L, LE>;
     constexpr int G = THREADS / S::P;
     size_t a = (size_t)G * S::STRIDE * sizeof(T);
     size_t red = G > 1 ? (size_t)S::N * sizeof(double) : 0;
