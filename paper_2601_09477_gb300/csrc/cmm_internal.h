@@ -41,6 +41,7 @@ struct SketchPlan {
     size_t off_At, off_Bp, off_partial, off_Z, off_tab, total;
     bool prep_A, prep_B;   // whether A / B are converted into the workspace
     int64_t ldat, ldbp;    // leading dimensions of the operands the sketch reads
+    bool tmem;             // use the TMEM variant of the FP32 kernel
 };
 
 // Plan of one cmm_backward call (mean-estimator adjoint).
@@ -86,6 +87,14 @@ cudaError_t launch_sketch_f64(const SketchPlan &pl, const double *At, const doub
                               cudaStream_t s);
 cudaError_t launch_finish(const double *partial, int nchunks, int d, int L, double *Z,
                           double *R, cudaStream_t s);
+// TMEM variant of the FP32 sketch kernel (2^14-point slices)
+bool sketch_tm_supported(int prec, int Llo);
+int sketch_tm_threads();
+size_t sketch_tm_smem();
+cudaError_t launch_sketch_tm(const SketchPlan &pl, const float *At, const float *Bp, int64_t m,
+                             int64_t k, int64_t p, int d, const HashParams &hp,
+                             const uint32_t *tabA, const uint32_t *tabB, double *partial,
+                             cudaStream_t s);
 int sketch_threads_f32(int Llo);
 int sketch_threads_f64(int Llo);
 size_t sketch_smem_f32(int Llo);

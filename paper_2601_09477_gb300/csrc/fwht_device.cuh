@@ -28,7 +28,7 @@ template <typename T, int L, int LE>
 struct PadOf {
     // 4 pad words per 32-word row for FP32 transforms of 2^10 and more (vector
     // rows in round 0); 1 otherwise (several groups share a warp below 2^10)
-    static constexpr int value = (sizeof(T) == 4 && LE == 5 && L >= 10) ? 4 : 1;
+    static constexpr int value = (sizeof(T) == 4 && LE >= 5 && L >= 10) ? 4 : 1;
 };
 
 template <typename T, int L, int LE>

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -121,6 +122,18 @@ int check_sizes(int64_t m, int64_t k, int64_t p) {
     return CMM_OK;
 }
 
+// The FP32 sketch of 2^14-point slices runs the TMEM kernel unless the
+// environment sets CMM_SKETCH_KERNEL=regs (the register-only kernel; both are
+// kept and tested against the oracle).
+bool use_tmem_kernel() {
+    static int cached = -1;
+    if (cached < 0) {
+        const char *v = std::getenv("CMM_SKETCH_KERNEL");
+        cached = (v && std::strcmp(v, "regs") == 0) ? 0 : 1;
+    }
+    return cached == 1;
+}
+
 // ---- sketch planning -------------------------------------------------------
 bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int prec, int transA,
                  int64_t lda, int64_t ldb, SketchPlan &pl) {
@@ -131,12 +144,14 @@ bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int p
     const int maxLlo = f64 ? kMaxLloF64 : kMaxLloF32;
     pl.Llo = std::min(L, maxLlo);
     pl.C = 1 << (L - pl.Llo);
-    pl.threads = f64 ? sketch_threads_f64(pl.Llo) : sketch_threads_f32(pl.Llo);
-    pl.smem = f64 ? sketch_smem_f64(pl.Llo) : sketch_smem_f32(pl.Llo);
-    const int LE = std::min(pl.Llo, f64 ? 4 : 5);
+    pl.tmem = sketch_tm_supported(prec, pl.Llo) && use_tmem_kernel();
+    pl.threads = pl.tmem ? sketch_tm_threads()
+                         : (f64 ? sketch_threads_f64(pl.Llo) : sketch_threads_f32(pl.Llo));
+    pl.smem = pl.tmem ? sketch_tm_smem() : (f64 ? sketch_smem_f64(pl.Llo) : sketch_smem_f32(pl.Llo));
+    const int LE = pl.tmem ? 7 : std::min(pl.Llo, f64 ? 4 : 5);
     const int P = (1 << pl.Llo) >> LE;
     const int G = pl.threads / P;
-    const int per_sm = pl.threads >= 512 ? 1 : 2;
+    const int per_sm = (pl.tmem || pl.threads < 512) ? 2 : 1;
     const int64_t slots = (int64_t)num_sms() * per_sm;
     const int64_t items = (int64_t)d * pl.C;
 
@@ -259,6 +274,9 @@ int run_sketch(const void *A, int64_t lda, int transA, const void *B, int64_t ld
         if (prec == CMM_PREC_F64)
             e = launch_sketch_f64(pl, (const double *)At, (const double *)Bp, m, k, p, hs->d, hp,
                                   tabA, tabB, partial, s);
+        else if (pl.tmem)
+            e = launch_sketch_tm(pl, (const float *)At, (const float *)Bp, m, k, p, hs->d, hp,
+                                 tabA, tabB, partial, s);
         else
             e = launch_sketch_f32(pl, (const float *)At, (const float *)Bp, m, k, p, hs->d, hp,
                                   tabA, tabB, partial, s);

@@ -72,11 +72,10 @@ __device__ __forceinline__ void scatter_column(T *Sg, const T *__restrict__ col,
 }
 
 // scatter one column using the packed (padded word | sign << 31) table
-template <typename T, int L, int LE>
+template <typename T, int L, int LE, int B = 8>
 __device__ __forceinline__ void scatter_table(T *Sg, const T *__restrict__ col,
                                               const uint32_t *__restrict__ tab, int64_t n, int q) {
     constexpr int P = FwhtShape<T, L, LE>::P;
-    constexpr int B = 8;
     int64_t i = q;
     for (; i + (B - 1) * (int64_t)P < n; i += B * (int64_t)P) {
         T val[B];

@@ -1,0 +1,220 @@
+// sketch_tm.cu -- FP32 sketch kernel for 2^14-point slices with the
+// transformed sketch and the accumulator in tensor memory (TMEM).
+//
+// Same work item and mathematics as sketch_kernel (Algorithm 1's loop over t,
+// frequency-split FWHT, FP32 multiply-accumulate, FP64 partial per block):
+// one CTA = (repetition r, frequency slice u_hi, block of inner indices).
+// What differs is the register blocking.  A CTA of 128 threads transforms the
+// 2^14-point slice with 128 values per thread, so the 14 butterfly stages take
+// two register rounds of 7 bits (one shared-memory round trip between them,
+// instead of two with 32 values per thread).  That leaves no registers for
+// H x_t and for the running sum Z, so both live in TMEM: each thread owns its
+// lane's 256 columns (128 for H x_t, 128 for Z) and moves them with
+// tcgen05.ld / tcgen05.st.  Two CTAs fit on an SM (2 x 256 TMEM columns),
+// each with its own barriers, so one CTA's scatter overlaps the other's
+// butterflies.
+//
+// Layout of the slice in shared memory: element u at word u + 4 * (u >> 7).
+// Round 0: thread q holds u = 128 q + j (a contiguous, 16-byte aligned row of
+// 128 words, read and written as float4); round 1: u = q + 128 j (the 32
+// lanes of a warp read 32 consecutive words).  Both are bank-conflict free.
+#include "cmm_internal.h"
+#include "fwht_device.cuh"
+#include "sketch_impl.cuh"
+
+namespace cmm {
+
+namespace {
+
+constexpr int kTmL = 14;
+constexpr int kTmLE = 7;
+constexpr int kTmE = 1 << kTmLE;           // values per thread
+constexpr int kTmP = (1 << kTmL) / kTmE;   // threads per CTA
+constexpr int kTmStride = (1 << kTmL) + 4 * ((1 << kTmL) >> kTmLE);
+constexpr size_t kTmSmem = 100 * 1024;     // >= 2/5 of an SM's shared memory: at most 2 CTAs per SM
+constexpr uint32_t kTmCols = 256;          // 128 columns H x_t + 128 columns Z per lane
+
+static_assert(kTmP == 128, "one TMEM lane per thread");
+static_assert(kTmStride * 4 + 16 <= (int)kTmSmem, "slice must fit");
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t addr, float (&x)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(addr)
+        : "memory");
+#pragma unroll
+    for (int e = 0; e < 16; ++e) x[e] = __uint_as_float(r[e]);
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t addr, const float *x) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n\t"
+        "tcgen05.wait::st.sync.aligned;"
+        :
+        : "r"(addr), "r"(__float_as_uint(x[0])), "r"(__float_as_uint(x[1])),
+          "r"(__float_as_uint(x[2])), "r"(__float_as_uint(x[3])), "r"(__float_as_uint(x[4])),
+          "r"(__float_as_uint(x[5])), "r"(__float_as_uint(x[6])), "r"(__float_as_uint(x[7])),
+          "r"(__float_as_uint(x[8])), "r"(__float_as_uint(x[9])), "r"(__float_as_uint(x[10])),
+          "r"(__float_as_uint(x[11])), "r"(__float_as_uint(x[12])), "r"(__float_as_uint(x[13])),
+          "r"(__float_as_uint(x[14])), "r"(__float_as_uint(x[15]))
+        : "memory");
+}
+
+// the 2^14-point FWHT of the slice S in two register rounds; result in v
+// with v[j] = element q + 128 j; the slice is left zeroed
+__device__ __forceinline__ void tm_fwht(float *S, float (&v)[kTmE], int q) {
+    float4 *row = reinterpret_cast<float4 *>(S + 132 * q);
+#pragma unroll
+    for (int c = 0; c < kTmE / 4; ++c) {
+        const float4 w = row[c];
+        v[4 * c] = w.x;
+        v[4 * c + 1] = w.y;
+        v[4 * c + 2] = w.z;
+        v[4 * c + 3] = w.w;
+    }
+    reg_fwht_f32<kTmE, kTmLE>(v);
+#pragma unroll
+    for (int c = 0; c < kTmE / 4; ++c)
+        row[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kTmE; ++j) v[j] = S[q + 132 * j];
+    reg_fwht_f32<kTmE, kTmLE>(v);
+#pragma unroll
+    for (int j = 0; j < kTmE; ++j) S[q + 132 * j] = 0.f;
+}
+
+__global__ void __launch_bounds__(kTmP, 2)
+sketch_tm_kernel(const float *__restrict__ At, int64_t ldat, const float *__restrict__ Bp,
+                 int64_t ldbp, int64_t m, int64_t k, int64_t p, int Lfull, int C, int64_t chunk,
+                 int d, const uint32_t *__restrict__ tabA, const uint32_t *__restrict__ tabB,
+                 double *__restrict__ partial) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *S = reinterpret_cast<float *>(smem_raw);
+    uint32_t *s_taddr = reinterpret_cast<uint32_t *>(smem_raw + kTmStride * sizeof(float));
+    const int q = threadIdx.x;
+    const int warp = q >> 5;
+
+    int item = blockIdx.x;
+    const uint32_t u_hi = (uint32_t)(item % C);
+    item /= C;
+    const int r = item % d;
+    const int64_t blk = item / d;
+    const int64_t t0 = blk * chunk;
+    const int64_t t1 = (t0 + chunk < k) ? t0 + chunk : k;
+    const int64_t b = (int64_t)1 << Lfull;
+    const int64_t slot = (int64_t)r * C + u_hi;
+    const uint32_t *tA = tabA + slot * m;
+    const uint32_t *tB = tabB + slot * p;
+    double *out = partial + (blk * d + r) * b + (int64_t)u_hi * (1 << kTmL);
+
+    if (warp == 0) {
+        asm volatile(
+            "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n\t"
+            "tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;"
+            :
+            : "r"(smem_addr(s_taddr)), "r"(kTmCols)
+            : "memory");
+    }
+    for (int i = q; i < kTmStride; i += kTmP) S[i] = 0.f;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // this warp's lanes: 32 * warp .. 32 * warp + 31; columns [0,128) H x, [128,256) Z
+    const uint32_t tx = *s_taddr + ((uint32_t)(32 * warp) << 16);
+    const uint32_t tz = tx + 128;
+    {
+        float zero[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) zero[e] = 0.f;
+#pragma unroll
+        for (int c = 0; c < kTmE / 16; ++c) tmem_st16(tz + 16 * c, zero);
+    }
+
+    float v[kTmE];
+    for (int64_t t = t0; t < t1; ++t) {
+        scatter_table<float, kTmL, kTmLE, 16>(S, At + t * ldat, tA, m, q);
+        __syncthreads();
+        tm_fwht(S, v, q);
+#pragma unroll
+        for (int c = 0; c < kTmE / 16; ++c) tmem_st16(tx + 16 * c, v + 16 * c);
+        __syncthreads();
+        scatter_table<float, kTmL, kTmLE, 16>(S, Bp + t * ldbp, tB, p, q);
+        __syncthreads();
+        tm_fwht(S, v, q);
+#pragma unroll
+        for (int c = 0; c < kTmE / 16; ++c) {
+            float xs[16], zs[16];
+            tmem_ld16(tx + 16 * c, xs);
+            tmem_ld16(tz + 16 * c, zs);
+#pragma unroll
+            for (int e = 0; e < 16; e += 2) {
+                const float2 acc = __ffma2_rn(make_float2(xs[e], xs[e + 1]),
+                                              make_float2(v[16 * c + e], v[16 * c + e + 1]),
+                                              make_float2(zs[e], zs[e + 1]));
+                zs[e] = acc.x;
+                zs[e + 1] = acc.y;
+            }
+            tmem_st16(tz + 16 * c, zs);
+        }
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int c = 0; c < kTmE / 16; ++c) {
+        float zs[16];
+        tmem_ld16(tz + 16 * c, zs);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) out[q + 128 * (16 * c + e)] = (double)zs[e];
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                     :
+                     : "r"(*s_taddr), "r"(kTmCols)
+                     : "memory");
+    }
+}
+
+}  // namespace
+
+bool sketch_tm_supported(int prec, int Llo) { return prec == CMM_PREC_F32 && Llo == kTmL; }
+int sketch_tm_threads() { return kTmP; }
+size_t sketch_tm_smem() { return kTmSmem; }
+
+cudaError_t launch_sketch_tm(const SketchPlan &pl, const float *At, const float *Bp, int64_t m,
+                             int64_t k, int64_t p, int d, const HashParams &hp,
+                             const uint32_t *tabA, const uint32_t *tabB, double *partial,
+                             cudaStream_t s) {
+    const int64_t n = (int64_t)d * pl.C * (m + p);
+    int64_t g = (n + 255) / 256;
+    if (g > 152 * 32) g = 152 * 32;
+    if (g < 1) g = 1;
+    sketch_table_kernel<float, kTmL, kTmLE><<<(unsigned)g, 256, 0, s>>>(
+        hp, d, pl.L, kTmL, pl.C, m, p, const_cast<uint32_t *>(tabA), const_cast<uint32_t *>(tabB));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sketch_tm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kTmSmem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (int64_t)pl.nchunks * d * pl.C;
+    sketch_tm_kernel<<<(unsigned)blocks, kTmP, kTmSmem, s>>>(At, pl.ldat, Bp, pl.ldbp, m, k, p,
+                                                             pl.L, pl.C, pl.chunk, d, tabA, tabB,
+                                                             partial);
+    return cudaGetLastError();
+}
+
+}  // namespace cmm

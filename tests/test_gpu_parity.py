@@ -63,6 +63,37 @@ def test_sketch_matches_oracle(cmm, prec, shape):
     assert err <= TOL[prec], err
 
 
+_REGS_SCRIPT = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_2601_09477_gb300 import cmm
+m, k, p, L, d = (int(x) for x in sys.argv[2:7])
+g = np.random.default_rng(m + k)
+A = g.standard_normal((m, k)); B = g.standard_normal((k, p))
+h = cmm.make_hashes(77 + L, d, L)
+R = cmm.sketch(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), h, prec="f32")
+np.savez(sys.argv[7], A=A, B=B, R=R.cpu().numpy(), hp=h.params)
+"""
+
+
+@pytest.mark.parametrize("shape", [(700, 260, 650, 14, 3), (300, 70, 500, 16, 2)])
+def test_register_only_sketch_kernel(cmm, shape, tmp_path):
+    # the FP32 2^14-slice sketch has a TMEM kernel (default) and a register-only
+    # kernel (CMM_SKETCH_KERNEL=regs); the second runs in a fresh process
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = str(tmp_path / "regs.npz")
+    env = dict(os.environ, CMM_SKETCH_KERNEL="regs")
+    subprocess.run([sys.executable, "-c", _REGS_SCRIPT, root] + [str(x) for x in shape] + [out],
+                   check=True, env=env)
+    z = np.load(out)
+    m, k, p, L, d = shape
+    Ro = orc.compress(z["A"], z["B"], z["hp"], L, nthreads=8)
+    assert np.abs(z["R"] - Ro).max() / _norm_scale(z["A"], z["B"]) <= TOL["f32"]
+
+
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32, torch.bfloat16])
 @pytest.mark.parametrize("transA", [False, True])
