@@ -156,18 +156,20 @@ bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int p
     const int64_t items = (int64_t)d * pl.C;
 
     // blocks of the inner index: at most 256 t per group (bounded FP32
-    // accumulation), otherwise as few blocks as fill the GPU evenly
+    // accumulation); otherwise the count that minimises the modelled time
+    // waves * (t per group + a fixed per-CTA cost of ~2 t for the partial
+    // write-out and set-up), preferring fewer blocks on ties
     const int64_t kk = std::max<int64_t>(k, 1);
     const int64_t nc_min = std::max<int64_t>(1, (kk + 256 * G - 1) / (256 * G));
     const int64_t nc_max = std::max<int64_t>(nc_min, (kk + G - 1) / G);
     int64_t best = nc_min;
-    double best_eff = -1.0;
+    double best_cost = 1e300;
     for (int64_t nc = nc_min; nc <= std::min(nc_max, nc_min + 8 * slots); ++nc) {
-        const int64_t total = items * nc;
-        const int64_t waves = (total + slots - 1) / slots;
-        const double eff = (double)total / (double)(waves * slots);
-        if (eff > best_eff + 0.005) {
-            best_eff = eff;
+        const int64_t waves = (items * nc + slots - 1) / slots;
+        const int64_t per_group = ((kk + nc - 1) / nc + G - 1) / G;
+        const double cost = (double)waves * (double)(per_group + 2);
+        if (cost < best_cost * 0.995) {
+            best_cost = cost;
             best = nc;
         }
     }
