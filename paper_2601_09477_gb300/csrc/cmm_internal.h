@@ -22,6 +22,10 @@ struct HashParams {
     HashRep rep[CMM_MAX_D];
 };
 
+// One scatter-table word: padded shared-memory index of the bucket in the low
+// 15 bits (slices of at most 2^14 points plus padding), the sign in bit 15.
+using tab_t = uint16_t;
+
 // Largest transform slice one CTA holds, per butterfly precision.
 constexpr int kMaxLloF32 = 14;   // 2^14 FP32 = 64 KiB of shared memory
 constexpr int kMaxLloF64 = 13;   // 2^13 FP64 = 64 KiB
@@ -79,11 +83,11 @@ cudaError_t launch_prep_B(const void *B, int64_t ldb, int dtype, int prec,
 // launcher when not null)
 cudaError_t launch_sketch_f32(const SketchPlan &pl, const float *At, const float *Bp,
                               int64_t m, int64_t k, int64_t p, int d, const HashParams &hp,
-                              const uint32_t *tabA, const uint32_t *tabB, double *partial,
+                              const tab_t *tabA, const tab_t *tabB, double *partial,
                               cudaStream_t s);
 cudaError_t launch_sketch_f64(const SketchPlan &pl, const double *At, const double *Bp,
                               int64_t m, int64_t k, int64_t p, int d, const HashParams &hp,
-                              const uint32_t *tabA, const uint32_t *tabB, double *partial,
+                              const tab_t *tabA, const tab_t *tabB, double *partial,
                               cudaStream_t s);
 cudaError_t launch_finish(const double *partial, int nchunks, int d, int L, double *Z,
                           double *R, cudaStream_t s);
@@ -93,7 +97,7 @@ int sketch_tm_threads();
 size_t sketch_tm_smem();
 cudaError_t launch_sketch_tm(const SketchPlan &pl, const float *At, const float *Bp, int64_t m,
                              int64_t k, int64_t p, int d, const HashParams &hp,
-                             const uint32_t *tabA, const uint32_t *tabB, double *partial,
+                             const tab_t *tabA, const tab_t *tabB, double *partial,
                              cudaStream_t s);
 int sketch_threads_f32(int Llo);
 int sketch_threads_f64(int Llo);

@@ -193,7 +193,7 @@ bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int p
     pl.off_Z = off;
     off += align_up((size_t)d * b * sizeof(double));
     pl.off_tab = off;
-    off += align_up((size_t)d * pl.C * (m + p) * sizeof(uint32_t));
+    off += align_up((size_t)d * pl.C * (m + p) * sizeof(tab_t));
     pl.total = off;
     return true;
 }
@@ -271,8 +271,8 @@ int run_sketch(const void *A, int64_t lda, int transA, const void *B, int64_t ld
     double *Z = reinterpret_cast<double *>(base + pl.off_Z);
     {
         Span sp(prec == CMM_PREC_F64 ? "sketch_f64" : "sketch_f32", s);
-        const uint32_t *tabA = reinterpret_cast<const uint32_t *>(base + pl.off_tab);
-        const uint32_t *tabB = tabA + (size_t)hs->d * pl.C * m;
+        const tab_t *tabA = reinterpret_cast<const tab_t *>(base + pl.off_tab);
+        const tab_t *tabB = tabA + (size_t)hs->d * pl.C * m;
         if (prec == CMM_PREC_F64)
             e = launch_sketch_f64(pl, (const double *)At, (const double *)Bp, m, k, p, hs->d, hp,
                                   tabA, tabB, partial, s);

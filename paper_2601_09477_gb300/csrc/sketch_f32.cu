@@ -12,8 +12,8 @@ struct F32Cfg {
 
 template <int L>
 cudaError_t run(const SketchPlan &pl, const float *At, const float *Bp, int64_t m, int64_t k,
-                int64_t p, int d, const HashParams &hp, const uint32_t *tabA,
-                const uint32_t *tabB, double *partial, cudaStream_t s) {
+                int64_t p, int d, const HashParams &hp, const tab_t *tabA,
+                const tab_t *tabB, double *partial, cudaStream_t s) {
     return launch_sketch_inst<float, float, L, F32Cfg<L>::LE, F32Cfg<L>::THREADS>(
         pl, At, Bp, m, k, p, d, hp, tabA, tabB, partial, s);
 }
@@ -46,7 +46,7 @@ size_t sketch_smem_f32(int Llo) {
 
 cudaError_t launch_sketch_f32(const SketchPlan &pl, const float *At, const float *Bp, int64_t m,
                               int64_t k, int64_t p, int d, const HashParams &hp,
-                              const uint32_t *tabA, const uint32_t *tabB, double *partial,
+                              const tab_t *tabA, const tab_t *tabB, double *partial,
                               cudaStream_t s) {
     switch (pl.Llo) {
 #define CASE(L) case L: return run<L>(pl, At, Bp, m, k, p, d, hp, tabA, tabB, partial, s);

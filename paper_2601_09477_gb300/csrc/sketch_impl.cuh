@@ -74,23 +74,23 @@ __device__ __forceinline__ void scatter_column(T *Sg, const T *__restrict__ col,
 // scatter one column using the packed (padded word | sign << 31) table
 template <typename T, int L, int LE, int B = 8>
 __device__ __forceinline__ void scatter_table(T *Sg, const T *__restrict__ col,
-                                              const uint32_t *__restrict__ tab, int64_t n, int q) {
+                                              const tab_t *__restrict__ tab, int64_t n, int q) {
     constexpr int P = FwhtShape<T, L, LE>::P;
     int64_t i = q;
     for (; i + (B - 1) * (int64_t)P < n; i += B * (int64_t)P) {
         T val[B];
-        uint32_t w[B];
+        tab_t w[B];
 #pragma unroll
         for (int e = 0; e < B; ++e) {
             val[e] = ld_stream(col + i + e * (int64_t)P);
             w[e] = __ldg(tab + i + e * (int64_t)P);
         }
 #pragma unroll
-        for (int e = 0; e < B; ++e) atomicAdd(Sg + (w[e] & 0x7fffffffu), neg_if(val[e], w[e] >> 31));
+        for (int e = 0; e < B; ++e) atomicAdd(Sg + (w[e] & 0x7fffu), neg_if(val[e], (uint32_t)(w[e] >> 15)));
     }
     for (; i < n; i += P) {
-        const uint32_t w = __ldg(tab + i);
-        atomicAdd(Sg + (w & 0x7fffffffu), neg_if(ld_stream(col + i), w >> 31));
+        const tab_t w = __ldg(tab + i);
+        atomicAdd(Sg + (w & 0x7fffu), neg_if(ld_stream(col + i), (uint32_t)(w >> 15)));
     }
 }
 
@@ -103,8 +103,8 @@ __device__ __forceinline__ void sketch_block(const T *__restrict__ At, int64_t l
                                              const T *__restrict__ Bp, int64_t ldbp, int64_t m,
                                              int64_t p, int Lfull, uint32_t u_hi, int64_t t0,
                                              int64_t t1, const HashRep &H,
-                                             const uint32_t *__restrict__ tabA,
-                                             const uint32_t *__restrict__ tabB,
+                                             const tab_t *__restrict__ tabA,
+                                             const tab_t *__restrict__ tabB,
                                              double *__restrict__ out, unsigned char *smem_raw) {
     using S = FwhtShape<T, L, LE>;
     constexpr int E = S::E, P = S::P, G = THREADS / P;
@@ -190,8 +190,8 @@ template <typename T, typename TZ, int L, int LE, int THREADS>
 __global__ void __launch_bounds__(THREADS, (THREADS >= 512 ? 1 : 2))
 sketch_kernel(const T *__restrict__ At, int64_t ldat, const T *__restrict__ Bp, int64_t ldbp,
               int64_t m, int64_t k, int64_t p, int Lfull, int C, int64_t chunk, int d,
-              const __grid_constant__ HashParams hp, const uint32_t *__restrict__ tabA,
-              const uint32_t *__restrict__ tabB, double *__restrict__ partial) {
+              const __grid_constant__ HashParams hp, const tab_t *__restrict__ tabA,
+              const tab_t *__restrict__ tabB, double *__restrict__ partial) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int item = blockIdx.x;
     const uint32_t u_hi = (uint32_t)(item % C);
@@ -213,7 +213,7 @@ sketch_kernel(const T *__restrict__ At, int64_t ldat, const T *__restrict__ Bp, 
 template <typename T, int L, int LE>
 __global__ void sketch_table_kernel(const __grid_constant__ HashParams hp, int d, int Lfull,
                                     int Llo, int C, int64_t m, int64_t p,
-                                    uint32_t *__restrict__ tabA, uint32_t *__restrict__ tabB) {
+                                    tab_t *__restrict__ tabA, tab_t *__restrict__ tabB) {
     const int shift = 64 - Lfull;
     const int64_t nA = (int64_t)d * C * m, n = nA + (int64_t)d * C * p;
     const uint32_t lo_mask = (1u << Llo) - 1u;
@@ -230,7 +230,7 @@ __global__ void sketch_table_kernel(const __grid_constant__ HashParams hp, int d
         const uint32_t h = isA ? mas_hash(H.a1, H.c1, x, shift) : mas_hash(H.a2, H.c2, x, shift);
         const uint32_t sb = isA ? mas_sign_bit(H.as1, H.cs1, x) : mas_sign_bit(H.as2, H.cs2, x);
         const uint32_t neg = sb ^ (__popc((h >> Llo) & u_hi) & 1u);
-        const uint32_t w = (uint32_t)pad_index<T, L, LE>((int)(h & lo_mask)) | (neg << 31);
+        const tab_t w = (tab_t)(pad_index<T, L, LE>((int)(h & lo_mask)) | (neg << 15));
         if (isA)
             tabA[f] = w;
         else
@@ -242,7 +242,7 @@ __global__ void sketch_table_kernel(const __grid_constant__ HashParams hp, int d
 template <typename T, typename TZ, int L, int LE, int THREADS>
 cudaError_t launch_sketch_inst(const SketchPlan &pl, const T *At, const T *Bp, int64_t m,
                                int64_t k, int64_t p, int d, const HashParams &hp,
-                               const uint32_t *tabA, const uint32_t *tabB, double *partial,
+                               const tab_t *tabA, const tab_t *tabB, double *partial,
                                cudaStream_t s) {
     if (tabA) {
         const int64_t n = (int64_t)d * pl.C * (m + p);
@@ -250,8 +250,8 @@ cudaError_t launch_sketch_inst(const SketchPlan &pl, const T *At, const T *Bp, i
         if (g > 152 * 32) g = 152 * 32;
         if (g < 1) g = 1;
         sketch_table_kernel<T, L, LE><<<(unsigned)g, 256, 0, s>>>(hp, d, pl.L, L, pl.C, m, p,
-                                                              const_cast<uint32_t *>(tabA),
-                                                              const_cast<uint32_t *>(tabB));
+                                                              const_cast<tab_t *>(tabA),
+                                                              const_cast<tab_t *>(tabB));
         cudaError_t e0 = cudaGetLastError();
         if (e0 != cudaSuccess) return e0;
     }

@@ -31,7 +31,10 @@ constexpr int kTmLE = 7;
 constexpr int kTmE = 1 << kTmLE;           // values per thread
 constexpr int kTmP = (1 << kTmL) / kTmE;   // threads per CTA
 constexpr int kTmStride = (1 << kTmL) + 4 * ((1 << kTmL) >> kTmLE);
-constexpr size_t kTmSmem = 100 * 1024;     // >= 2/5 of an SM's shared memory: at most 2 CTAs per SM
+// shared memory: the slice plus the TMEM address word.  Registers (about 250
+// per thread) hold the SM to two CTAs, matching the 2 x 256 TMEM columns; the
+// rest of the unified L1 caches the scatter tables.
+constexpr size_t kTmSmem = kTmStride * sizeof(float) + 16;
 constexpr uint32_t kTmCols = 256;          // 128 columns H x_t + 128 columns Z per lane
 
 static_assert(kTmP == 128, "one TMEM lane per thread");
@@ -98,7 +101,7 @@ __device__ __forceinline__ void tm_fwht(float *S, float (&v)[kTmE], int q) {
 __global__ void __launch_bounds__(kTmP, 2)
 sketch_tm_kernel(const float *__restrict__ At, int64_t ldat, const float *__restrict__ Bp,
                  int64_t ldbp, int64_t m, int64_t k, int64_t p, int Lfull, int C, int64_t chunk,
-                 int d, const uint32_t *__restrict__ tabA, const uint32_t *__restrict__ tabB,
+                 int d, const tab_t *__restrict__ tabA, const tab_t *__restrict__ tabB,
                  double *__restrict__ partial) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *S = reinterpret_cast<float *>(smem_raw);
@@ -115,8 +118,8 @@ sketch_tm_kernel(const float *__restrict__ At, int64_t ldat, const float *__rest
     const int64_t t1 = (t0 + chunk < k) ? t0 + chunk : k;
     const int64_t b = (int64_t)1 << Lfull;
     const int64_t slot = (int64_t)r * C + u_hi;
-    const uint32_t *tA = tabA + slot * m;
-    const uint32_t *tB = tabB + slot * p;
+    const tab_t *tA = tabA + slot * m;
+    const tab_t *tB = tabB + slot * p;
     double *out = partial + (blk * d + r) * b + (int64_t)u_hi * (1 << kTmL);
 
     if (warp == 0) {
@@ -197,14 +200,14 @@ size_t sketch_tm_smem() { return kTmSmem; }
 
 cudaError_t launch_sketch_tm(const SketchPlan &pl, const float *At, const float *Bp, int64_t m,
                              int64_t k, int64_t p, int d, const HashParams &hp,
-                             const uint32_t *tabA, const uint32_t *tabB, double *partial,
+                             const tab_t *tabA, const tab_t *tabB, double *partial,
                              cudaStream_t s) {
     const int64_t n = (int64_t)d * pl.C * (m + p);
     int64_t g = (n + 255) / 256;
     if (g > 152 * 32) g = 152 * 32;
     if (g < 1) g = 1;
     sketch_table_kernel<float, kTmL, kTmLE><<<(unsigned)g, 256, 0, s>>>(
-        hp, d, pl.L, kTmL, pl.C, m, p, const_cast<uint32_t *>(tabA), const_cast<uint32_t *>(tabB));
+        hp, d, pl.L, kTmL, pl.C, m, p, const_cast<tab_t *>(tabA), const_cast<tab_t *>(tabB));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(sketch_tm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
