@@ -79,7 +79,7 @@ def peaks():
 
 def source_hash():
     h = hashlib.sha256()
-    for name in ["sketch_impl.cuh", "fwht_device.cuh", "sketch_f32.cu"]:
+    for name in ["sketch_impl.cuh", "fwht_device.cuh", "sketch_f32.cu", "sketch_tm.cu"]:
         with open(os.path.join(ROOT, "paper_2601_09477_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
