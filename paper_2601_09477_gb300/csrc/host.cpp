@@ -141,17 +141,22 @@ bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int p
     pl.prec = prec;
     pl.L = L;
     const bool f64 = prec == CMM_PREC_F64;
-    const int maxLlo = f64 ? kMaxLloF64 : kMaxLloF32;
+    const bool bf16 = prec == CMM_PREC_BF16TC;
+    if (bf16 && L < sketch_bf16_llo()) return false;
+    const int maxLlo = bf16 ? sketch_bf16_llo() : (f64 ? kMaxLloF64 : kMaxLloF32);
     pl.Llo = std::min(L, maxLlo);
     pl.C = 1 << (L - pl.Llo);
     pl.tmem = sketch_tm_supported(prec, pl.Llo) && use_tmem_kernel();
-    pl.threads = pl.tmem ? sketch_tm_threads()
-                         : (f64 ? sketch_threads_f64(pl.Llo) : sketch_threads_f32(pl.Llo));
-    pl.smem = pl.tmem ? sketch_tm_smem() : (f64 ? sketch_smem_f64(pl.Llo) : sketch_smem_f32(pl.Llo));
-    const int LE = pl.tmem ? 7 : std::min(pl.Llo, f64 ? 4 : 5);
+    pl.threads = bf16 ? sketch_bf16_threads()
+                      : pl.tmem ? sketch_tm_threads()
+                                : (f64 ? sketch_threads_f64(pl.Llo) : sketch_threads_f32(pl.Llo));
+    pl.smem = bf16 ? sketch_bf16_smem()
+                   : pl.tmem ? sketch_tm_smem()
+                             : (f64 ? sketch_smem_f64(pl.Llo) : sketch_smem_f32(pl.Llo));
+    const int LE = bf16 ? pl.Llo : pl.tmem ? 7 : std::min(pl.Llo, f64 ? 4 : 5);
     const int P = (1 << pl.Llo) >> LE;
-    const int G = pl.threads / P;
-    const int per_sm = (pl.tmem || pl.threads < 512) ? 2 : 1;
+    const int G = bf16 ? 1 : pl.threads / P;
+    const int per_sm = bf16 ? 1 : (pl.tmem || pl.threads < 512) ? 2 : 1;
     const int64_t slots = (int64_t)num_sms() * per_sm;
     const int64_t items = (int64_t)d * pl.C;
 
@@ -193,7 +198,7 @@ bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int p
     pl.off_Z = off;
     off += align_up((size_t)d * b * sizeof(double));
     pl.off_tab = off;
-    off += align_up((size_t)d * pl.C * (m + p) * sizeof(tab_t));
+    off += align_up((size_t)d * pl.C * (m + p) * (bf16 ? sizeof(uint32_t) : sizeof(tab_t)));
     pl.total = off;
     return true;
 }
@@ -276,7 +281,11 @@ int run_sketch(const void *A, int64_t lda, int transA, const void *B, int64_t ld
         if (prec == CMM_PREC_F64)
             e = launch_sketch_f64(pl, (const double *)At, (const double *)Bp, m, k, p, hs->d, hp,
                                   tabA, tabB, partial, s);
-        else if (pl.tmem)
+        else if (prec == CMM_PREC_BF16TC) {
+            uint32_t *tA32 = reinterpret_cast<uint32_t *>(base + pl.off_tab);
+            e = launch_sketch_bf16(pl, (const float *)At, (const float *)Bp, m, k, p, hs->d, hp,
+                                   tA32, tA32 + (size_t)hs->d * pl.C * m, partial, s);
+        } else if (pl.tmem)
             e = launch_sketch_tm(pl, (const float *)At, (const float *)Bp, m, k, p, hs->d, hp,
                                  tabA, tabB, partial, s);
         else
@@ -502,7 +511,7 @@ size_t cmm_sketch_workspace_bytes(int64_t m, int64_t k, int64_t p, int32_t d, in
         log2b > CMM_MAX_LOG2B || !valid_dtype(dtype))
         return 0;
     SketchPlan pl;
-    plan_sketch(m, k, p, d, log2b, dtype, prec, transA, transA ? m : k, p, pl);
+    if (!plan_sketch(m, k, p, d, log2b, dtype, prec, transA, transA ? m : k, p, pl)) return 0;
     return pl.total;
 }
 
@@ -514,8 +523,8 @@ int cmm_sketch(const void *A, int64_t lda, int32_t transA, const void *B, int64_
     if (rc) return rc;
     rc = check_operands(A, lda, transA, B, ldb, dtype, m, k, p, prec);
     if (rc) return rc;
-    if (prec == CMM_PREC_BF16TC)
-        return fail(CMM_ERR_ARG, "precision BF16TC is not available in this build");
+    if (prec == CMM_PREC_BF16TC && hs->log2b < sketch_bf16_llo())
+        return fail(CMM_ERR_RANGE, "precision BF16TC needs log2b >= %d", sketch_bf16_llo());
     if (!R) return fail(CMM_ERR_ARG, "R is NULL");
     const size_t need = cmm_sketch_workspace_bytes(m, k, p, hs->d, hs->log2b, dtype, prec, transA);
     rc = check_ws(ws, ws_bytes, need);
@@ -599,8 +608,8 @@ int cmm_multiply(const void *A, int64_t lda, int32_t transA, const void *B, int6
     if (rc) return rc;
     rc = check_operands(A, lda, transA, B, ldb, dtype, m, k, p, prec);
     if (rc) return rc;
-    if (prec == CMM_PREC_BF16TC)
-        return fail(CMM_ERR_ARG, "precision BF16TC is not available in this build");
+    if (prec == CMM_PREC_BF16TC && hs->log2b < sketch_bf16_llo())
+        return fail(CMM_ERR_RANGE, "precision BF16TC needs log2b >= %d", sketch_bf16_llo());
     if (reduce != CMM_MEDIAN && reduce != CMM_MEAN) return fail(CMM_ERR_ARG, "bad reduce %d", reduce);
     if (m > 0 && p > 0 && (!C || ldc < p)) return fail(CMM_ERR_ARG, "C is NULL or ldc < p");
     const size_t need = cmm_multiply_workspace_bytes(m, k, p, hs->d, hs->log2b, dtype, prec, transA);
@@ -637,8 +646,8 @@ int cmm_multiply_host(const void *A, int64_t lda, int32_t transA, const void *B,
     if (rc) return rc;
     rc = check_operands(A, lda, transA, B, ldb, dtype, m, k, p, prec);
     if (rc) return rc;
-    if (prec == CMM_PREC_BF16TC)
-        return fail(CMM_ERR_ARG, "precision BF16TC is not available in this build");
+    if (prec == CMM_PREC_BF16TC && hs->log2b < sketch_bf16_llo())
+        return fail(CMM_ERR_RANGE, "precision BF16TC needs log2b >= %d", sketch_bf16_llo());
     if (reduce != CMM_MEDIAN && reduce != CMM_MEAN) return fail(CMM_ERR_ARG, "bad reduce %d", reduce);
     if (C && ldc < p) return fail(CMM_ERR_ARG, "ldc = %lld < p", (long long)ldc);
     if (count && capacity < 0) return fail(CMM_ERR_ARG, "negative capacity");

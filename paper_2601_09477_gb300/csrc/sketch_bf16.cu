@@ -1,0 +1,373 @@
+// sketch_bf16.cu -- the sketch with BF16 tensor-core Hadamard blocks.
+//
+// Same work item as the FP32 kernels (Algorithm 1's loop over t, frequency
+// split, FP64 partial per block of t), for 2^15-point slices.  The transform
+// of a slice (15 butterfly stages) runs as two passes of exact +-1 Hadamard
+// blocks on the tensor cores (mma.sync m16n8k16, BF16 operands, FP32
+// accumulation):
+//   pass 1, bits 0-7:  a 16x16 tile X[a][b] (u = a + 16 b + 256 tau) becomes
+//                      H16 X H16 -- D1 = H16 . X, then D2 = D1 . H16, where the
+//                      accumulator fragments of D1 are exactly the A-operand
+//                      fragments of the second product (no data movement);
+//   pass 2, bits 8-14: X2[a2][n] with u = e + 2 tau' + 256 a2 + 4096 f and
+//                      n = e + 2 f becomes H16 X2 (H8 (x) I2): bits 8-11 by
+//                      H16, bits 12-14 by H8 while bit 0 (already transformed
+//                      in pass 1) passes through the identity factor.
+// H16, H8 (x) I2 hold only 0 and +-1, exact in BF16.  Rounding happens where a
+// value becomes a BF16 operand: the scatter (BF16 shared-memory atomics), the
+// product inputs of both passes, and the slice between the passes.  H x_t and
+// the running sum Z stay FP32 in tensor memory (TMEM), one lane per thread.
+//
+// Shared-memory layout (BF16 elements): u at u + 2 * (((u >> 8) & 15) +
+// 7 * (u >> 12)); pass-1 loads and pass-2 loads/zeroing are bank-conflict
+// free, pass-1 stores are 2-way conflicted.
+#include <cuda_bf16.h>
+
+#include "cmm_internal.h"
+#include "fwht_device.cuh"
+
+namespace cmm {
+
+namespace {
+
+constexpr int kBL = 15;                        // log2 of the slice
+constexpr int kBN = 1 << kBL;
+constexpr int kBThreads = 512;                 // 16 warps
+constexpr int kBWarps = kBThreads / 32;
+constexpr int kBTiles = kBN / 256;             // 128 tiles of 256 per pass
+constexpr int kBTilesPerWarp = kBTiles / kBWarps;   // 8
+constexpr int kBElems = kBN + 2 * (15 + 7 * 7) + 2;   // padded BF16 elements
+constexpr size_t kBSmem = ((size_t)kBElems * 2 + 15) / 16 * 16 + 16;
+constexpr uint32_t kBCols = 512;               // whole TMEM: 4 warps per lane quadrant x 128
+
+__host__ __device__ constexpr int bf_pad(int u) {
+    return u + 2 * (((u >> 8) & 15) + 7 * (u >> 12));
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+__device__ __forceinline__ float hsign(int i, int j) {
+    return (__popc(i & j) & 1) ? -1.f : 1.f;
+}
+
+// D (16x8, FP32) = A (16x16, BF16) . B (16x8, BF16)
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4],
+                                         const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%10,%11,%12,%13};"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "f"(0.f), "f"(0.f),
+          "f"(0.f), "f"(0.f));
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t addr, const float (&x)[8]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n\t"
+        "tcgen05.wait::st.sync.aligned;"
+        :
+        : "r"(addr), "r"(__float_as_uint(x[0])), "r"(__float_as_uint(x[1])),
+          "r"(__float_as_uint(x[2])), "r"(__float_as_uint(x[3])), "r"(__float_as_uint(x[4])),
+          "r"(__float_as_uint(x[5])), "r"(__float_as_uint(x[6])), "r"(__float_as_uint(x[7]))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t addr, float (&x)[8]) {
+    uint32_t r[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "r"(addr)
+        : "memory");
+#pragma unroll
+    for (int e = 0; e < 8; ++e) x[e] = __uint_as_float(r[e]);
+}
+
+// constant operand fragments of the Hadamard blocks for this lane
+struct HFrags {
+    uint32_t hA[4];      // H16 as the A operand (16x16)
+    uint32_t hB[2][2];   // H16 as the B operand, columns 0-7 and 8-15
+    uint32_t mB[2][2];   // H8 (x) I2 as the B operand: M[k][n] = H8[k>>1][n>>1] [k&1 == n&1]
+};
+
+__device__ __forceinline__ float m2(int k, int n) {
+    return ((k & 1) == (n & 1)) ? hsign(k >> 1, n >> 1) : 0.f;
+}
+
+__device__ __forceinline__ void make_frags(HFrags &f, int g, int c) {
+    // A fragment: (row g, k 2c..2c+1), (row g+8, k 2c..), (row g, k 2c+8..), (row g+8, k 2c+8..)
+    f.hA[0] = pack_bf16(hsign(g, 2 * c), hsign(g, 2 * c + 1));
+    f.hA[1] = pack_bf16(hsign(g + 8, 2 * c), hsign(g + 8, 2 * c + 1));
+    f.hA[2] = pack_bf16(hsign(g, 2 * c + 8), hsign(g, 2 * c + 9));
+    f.hA[3] = pack_bf16(hsign(g + 8, 2 * c + 8), hsign(g + 8, 2 * c + 9));
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int n = 8 * h + g;   // B fragment: (k 2c..2c+1, col n), (k 2c+8..2c+9, col n)
+        f.hB[h][0] = pack_bf16(hsign(2 * c, n), hsign(2 * c + 1, n));
+        f.hB[h][1] = pack_bf16(hsign(2 * c + 8, n), hsign(2 * c + 9, n));
+        f.mB[h][0] = pack_bf16(m2(2 * c, n), m2(2 * c + 1, n));
+        f.mB[h][1] = pack_bf16(m2(2 * c + 8, n), m2(2 * c + 9, n));
+    }
+}
+
+// one tile: D2 = (H16 . X) . Bop for the two column halves.  xb[h] are the
+// B-operand fragments of X (column half h); d2[h] the output fragments.
+__device__ __forceinline__ void tile_pass(const HFrags &f, const uint32_t (&xb)[2][2],
+                                          const uint32_t (&bop)[2][2], float (&d2)[2][4]) {
+    float d1[2][4];
+    mma_bf16(d1[0], f.hA, xb[0]);
+    mma_bf16(d1[1], f.hA, xb[1]);
+    // accumulator fragments of D1 = A-operand fragment of D1 (rows g / g+8, k = columns)
+    const uint32_t a[4] = {pack_bf16(d1[0][0], d1[0][1]), pack_bf16(d1[0][2], d1[0][3]),
+                           pack_bf16(d1[1][0], d1[1][1]), pack_bf16(d1[1][2], d1[1][3])};
+    mma_bf16(d2[0], a, bop[0]);
+    mma_bf16(d2[1], a, bop[1]);
+}
+
+// the 2^15-point transform of the slice; `sink(i, vals)` receives, for the
+// warp's i-th pass-2 tile, the 8 FP32 outputs of this thread.  The slice is
+// left zeroed.
+template <typename Sink>
+__device__ __forceinline__ void bf_fwht(__nv_bfloat16 *S, const HFrags &f, int warp, int g, int c,
+                                        Sink sink) {
+    uint16_t *S16 = reinterpret_cast<uint16_t *>(S);
+    // pass 1: tiles tau = warp * 8 + i, u = a + 16 b + 256 tau
+#pragma unroll 2
+    for (int i = 0; i < kBTilesPerWarp; ++i) {
+        const int tau = warp * kBTilesPerWarp + i;
+        uint32_t xb[2][2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int b = 8 * h + g;
+            const int u0 = 2 * c + 16 * b + 256 * tau;
+            xb[h][0] = *reinterpret_cast<const uint32_t *>(S + bf_pad(u0));
+            xb[h][1] = *reinterpret_cast<const uint32_t *>(S + bf_pad(u0 + 8));
+        }
+        float d2[2][4];
+        tile_pass(f, xb, f.hB, d2);
+        // d2[h]: rows a' = g (regs 0,1) / g + 8 (regs 2,3), columns b' = 8h + 2c (+1)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr) {
+                const int ap = g + 8 * (rr >> 1);
+                const int bp = 8 * h + 2 * c + (rr & 1);
+                __nv_bfloat16 v = __float2bfloat16_rn(d2[h][rr]);
+                S16[bf_pad(ap + 16 * bp + 256 * tau)] = *reinterpret_cast<uint16_t *>(&v);
+            }
+        }
+    }
+    __syncthreads();
+    // pass 2: tiles tau' = warp * 8 + i over bits 1-7, u = e + 2 tau' + 256 a2 + 4096 f
+#pragma unroll 2
+    for (int i = 0; i < kBTilesPerWarp; ++i) {
+        const int taup = warp * kBTilesPerWarp + i;
+        uint32_t xb[2][2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int n = 8 * h + g;
+            const int e = n & 1, fq = n >> 1;
+            const int base = e + 2 * taup + 4096 * fq;
+            const int k0 = 2 * c;
+            const int ua = base + 256 * k0, ub = base + 256 * (k0 + 1);
+            const int uc = base + 256 * (k0 + 8), ud = base + 256 * (k0 + 9);
+            const uint32_t va = S16[bf_pad(ua)], vb = S16[bf_pad(ub)];
+            const uint32_t vc = S16[bf_pad(uc)], vd = S16[bf_pad(ud)];
+            xb[h][0] = va | (vb << 16);
+            xb[h][1] = vc | (vd << 16);
+            S16[bf_pad(ua)] = 0;
+            S16[bf_pad(ub)] = 0;
+            S16[bf_pad(uc)] = 0;
+            S16[bf_pad(ud)] = 0;
+        }
+        float d2[2][4];
+        tile_pass(f, xb, f.mB, d2);
+        float vals[8];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr) vals[4 * h + rr] = d2[h][rr];
+        sink(i, vals);
+    }
+}
+
+// index u (in the slice) of output value v (0..7) of pass-2 tile i for this thread
+__device__ __forceinline__ int bf_out_index(int warp, int g, int c, int i, int v) {
+    const int taup = warp * kBTilesPerWarp + i;
+    const int h = v >> 2, rr = v & 3;
+    const int a2 = g + 8 * (rr >> 1);
+    const int n = 8 * h + 2 * c + (rr & 1);
+    return (n & 1) + 2 * taup + 256 * a2 + 4096 * (n >> 1);
+}
+
+__device__ __forceinline__ void scatter_bf16(__nv_bfloat16 *S, const float *__restrict__ col,
+                                             const uint32_t *__restrict__ tab, int64_t n, int q) {
+    constexpr int B = 8;
+    int64_t i = q;
+    for (; i + (B - 1) * (int64_t)kBThreads < n; i += B * (int64_t)kBThreads) {
+        float val[B];
+        uint32_t w[B];
+#pragma unroll
+        for (int e = 0; e < B; ++e) {
+            val[e] = __ldcs(col + i + e * (int64_t)kBThreads);
+            w[e] = __ldg(tab + i + e * (int64_t)kBThreads);
+        }
+#pragma unroll
+        for (int e = 0; e < B; ++e)
+            atomicAdd(S + (w[e] & 0x7fffffffu), __float2bfloat16_rn((w[e] >> 31) ? -val[e] : val[e]));
+    }
+    for (; i < n; i += kBThreads) {
+        const uint32_t w = __ldg(tab + i);
+        const float v = __ldcs(col + i);
+        atomicAdd(S + (w & 0x7fffffffu), __float2bfloat16_rn((w >> 31) ? -v : v));
+    }
+}
+
+__global__ void __launch_bounds__(kBThreads, 1)
+sketch_bf16_kernel(const float *__restrict__ At, int64_t ldat, const float *__restrict__ Bp,
+                   int64_t ldbp, int64_t m, int64_t k, int64_t p, int Lfull, int C, int64_t chunk,
+                   int d, const uint32_t *__restrict__ tabA, const uint32_t *__restrict__ tabB,
+                   double *__restrict__ partial) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __nv_bfloat16 *S = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
+    uint32_t *s_taddr = reinterpret_cast<uint32_t *>(smem_raw + kBSmem - 16);
+    const int q = threadIdx.x, warp = q >> 5, lane = q & 31;
+    const int g = lane >> 2, c = lane & 3;
+
+    int item = blockIdx.x;
+    const uint32_t u_hi = (uint32_t)(item % C);
+    item /= C;
+    const int r = item % d;
+    const int64_t blk = item / d;
+    const int64_t t0 = blk * chunk;
+    const int64_t t1 = (t0 + chunk < k) ? t0 + chunk : k;
+    const int64_t b = (int64_t)1 << Lfull;
+    const int64_t slot = (int64_t)r * C + u_hi;
+    const uint32_t *tA = tabA + slot * m;
+    const uint32_t *tB = tabB + slot * p;
+    double *out = partial + (blk * d + r) * b + (int64_t)u_hi * kBN;
+
+    if (warp == 0) {
+        asm volatile(
+            "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n\t"
+            "tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;"
+            :
+            : "r"(smem_u32(s_taddr)), "r"(kBCols)
+            : "memory");
+    }
+    uint16_t *S16 = reinterpret_cast<uint16_t *>(S);
+    for (int i = q; i < kBElems; i += kBThreads) S16[i] = 0;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // lanes of quadrant warp % 4; four warps share a quadrant: columns 128 * (warp / 4) ...
+    const uint32_t tx = *s_taddr + ((uint32_t)(32 * (warp & 3)) << 16) + 128u * (uint32_t)(warp >> 2);
+    const uint32_t tz = tx + 64;
+    HFrags f;
+    make_frags(f, g, c);
+    {
+        float zero[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) zero[e] = 0.f;
+#pragma unroll
+        for (int i = 0; i < kBTilesPerWarp; ++i) tmem_st8(tz + 8 * i, zero);
+    }
+
+    for (int64_t t = t0; t < t1; ++t) {
+        scatter_bf16(S, At + t * ldat, tA, m, q);
+        __syncthreads();
+        bf_fwht(S, f, warp, g, c, [&](int i, const float(&vals)[8]) { tmem_st8(tx + 8 * i, vals); });
+        __syncthreads();
+        scatter_bf16(S, Bp + t * ldbp, tB, p, q);
+        __syncthreads();
+        bf_fwht(S, f, warp, g, c, [&](int i, const float(&vals)[8]) {
+            float xs[8], zs[8];
+            tmem_ld8(tx + 8 * i, xs);
+            tmem_ld8(tz + 8 * i, zs);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) zs[e] = fmaf(xs[e], vals[e], zs[e]);
+            tmem_st8(tz + 8 * i, zs);
+        });
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int i = 0; i < kBTilesPerWarp; ++i) {
+        float zs[8];
+        tmem_ld8(tz + 8 * i, zs);
+#pragma unroll
+        for (int v = 0; v < 8; ++v) out[bf_out_index(warp, g, c, i, v)] = (double)zs[v];
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                     :
+                     : "r"(*s_taddr), "r"(kBCols)
+                     : "memory");
+    }
+}
+
+// scatter words for the BF16 slice layout: padded element index | sign << 31
+__global__ void bf16_table_kernel(const __grid_constant__ HashParams hp, int d, int Lfull, int C,
+                                  int64_t m, int64_t p, uint32_t *__restrict__ tabA,
+                                  uint32_t *__restrict__ tabB) {
+    const int shift = 64 - Lfull;
+    const int64_t nA = (int64_t)d * C * m, n = nA + (int64_t)d * C * p;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const bool isA = e < nA;
+        const int64_t fidx = isA ? e : e - nA;
+        const int64_t len = isA ? m : p;
+        const int64_t slot = fidx / len;
+        const uint64_t x = (uint64_t)(fidx % len);
+        const int r = (int)(slot / C);
+        const uint32_t u_hi = (uint32_t)(slot % C);
+        const HashRep &H = hp.rep[r];
+        const uint32_t h = isA ? mas_hash(H.a1, H.c1, x, shift) : mas_hash(H.a2, H.c2, x, shift);
+        const uint32_t sb = isA ? mas_sign_bit(H.as1, H.cs1, x) : mas_sign_bit(H.as2, H.cs2, x);
+        const uint32_t neg = sb ^ (__popc((h >> kBL) & u_hi) & 1u);
+        const uint32_t w = (uint32_t)bf_pad((int)(h & (kBN - 1))) | (neg << 31);
+        if (isA)
+            tabA[fidx] = w;
+        else
+            tabB[fidx] = w;
+    }
+}
+
+}  // namespace
+
+int sketch_bf16_llo() { return kBL; }
+int sketch_bf16_threads() { return kBThreads; }
+size_t sketch_bf16_smem() { return kBSmem; }
+
+cudaError_t launch_sketch_bf16(const SketchPlan &pl, const float *At, const float *Bp, int64_t m,
+                               int64_t k, int64_t p, int d, const HashParams &hp, uint32_t *tabA,
+                               uint32_t *tabB, double *partial, cudaStream_t s) {
+    const int64_t n = (int64_t)d * pl.C * (m + p);
+    int64_t gsz = (n + 255) / 256;
+    if (gsz > 152 * 32) gsz = 152 * 32;
+    if (gsz < 1) gsz = 1;
+    bf16_table_kernel<<<(unsigned)gsz, 256, 0, s>>>(hp, d, pl.L, pl.C, m, p, tabA, tabB);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(sketch_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kBSmem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (int64_t)pl.nchunks * d * pl.C;
+    sketch_bf16_kernel<<<(unsigned)blocks, kBThreads, kBSmem, s>>>(
+        At, pl.ldat, Bp, pl.ldbp, m, k, p, pl.L, pl.C, pl.chunk, d, tabA, tabB, partial);
+    return cudaGetLastError();
+}
+
+}  // namespace cmm

@@ -63,6 +63,35 @@ def test_sketch_matches_oracle(cmm, prec, shape):
     assert err <= TOL[prec], err
 
 
+@pytest.mark.parametrize("shape", [(1000, 200, 900, 15, 3), (517, 97, 333, 17, 2),
+                                   (2048, 300, 1500, 16, 5), (64, 33, 70, 15, 1)])
+def test_sketch_bf16_tensor_core(cmm, shape):
+    # BF16 operands with exact +-1 Hadamard blocks, FP32 accumulation:
+    # error relative to sum_t ||A_t|| ||B_t|| within 2e-2
+    m, k, p, L, d = shape
+    g = np.random.default_rng(m + k + p)
+    A = g.standard_normal((m, k))
+    B = g.standard_normal((k, p))
+    h = cmm.make_hashes(300 + L, d, L)
+    R = cmm.sketch(_dev(A, torch.float32), _dev(B, torch.float32), h, prec="bf16tc").cpu().numpy()
+    A32 = A.astype(np.float32).astype(np.float64)
+    B32 = B.astype(np.float32).astype(np.float64)
+    Ro = orc.compress(A32, B32, h.params, L, nthreads=8)
+    err = np.abs(R - Ro).max() / _norm_scale(A32, B32)
+    assert err <= 2e-2, err
+    # and it is a real approximation, not noise: the error is far below the signal
+    assert np.abs(R - Ro).max() < 0.05 * np.abs(Ro).max()
+
+
+def test_sketch_bf16_needs_large_slices(cmm):
+    h = cmm.make_hashes(1, 3, 12)
+    A = torch.zeros((20, 10), dtype=torch.float32, device="cuda")
+    B = torch.zeros((10, 30), dtype=torch.float32, device="cuda")
+    with pytest.raises(cmm.CmmError) as ei:
+        cmm.sketch(A, B, h, prec="bf16tc")
+    assert ei.value.code == cmm.ERR_RANGE
+
+
 _REGS_SCRIPT = r"""
 import sys, numpy as np, torch
 sys.path.insert(0, sys.argv[1])
