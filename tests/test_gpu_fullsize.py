@@ -51,8 +51,10 @@ def test_planted_pm1_8192_exact(cmm):
     found = set(zip(I.cpu().tolist(), J.cpu().tolist()))
     planted = {(int(i), int(j)) for i, j in pairs} | {(int(j), int(i)) for i, j in pairs}
     assert sum(q in found for q in planted) >= 0.95 * len(planted)
+    # C_ii = n on the diagonal; one repetition's noise has sd about sqrt(||C||_F^2 / b)
+    # ~ n/2 here, so a median below n/2 has probability ~0.4% per entry
     diag = sum(1 for (i, j) in found if i == j)
-    assert diag == n          # C_ii = n on the diagonal, far above the noise
+    assert diag >= 0.99 * n
 
 
 @pytest.mark.parametrize("prec,tol", [("f32", 1e-5), ("bf16tc", 2e-2)])
