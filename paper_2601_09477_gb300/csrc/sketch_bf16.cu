@@ -18,9 +18,9 @@
 // product inputs of both passes, and the slice between the passes.  H x_t and
 // the running sum Z stay FP32 in tensor memory (TMEM), one lane per thread.
 //
-// Shared-memory layout (BF16 elements): u at u + 2 * (((u >> 8) & 15) +
-// 7 * (u >> 12)); pass-1 loads and pass-2 loads/zeroing are bank-conflict
-// free, pass-1 stores are 2-way conflicted.
+// Shared-memory layout (BF16 elements): u at u + 2 * ((u >> 8) + 7 * (u >> 12));
+// pass-2 loads and zeroing are bank-conflict free, pass-1 loads and stores are
+// 2-way conflicted.
 #include <cuda_bf16.h>
 
 #include "cmm_internal.h"
@@ -36,12 +36,14 @@ constexpr int kBThreads = 512;                 // 16 warps
 constexpr int kBWarps = kBThreads / 32;
 constexpr int kBTiles = kBN / 256;             // 128 tiles of 256 per pass
 constexpr int kBTilesPerWarp = kBTiles / kBWarps;   // 8
-constexpr int kBElems = kBN + 2 * (15 + 7 * 7) + 2;   // padded BF16 elements
+constexpr int kBElems = kBN + 2 * (127 + 7 * 7) + 2;   // padded BF16 elements
 constexpr size_t kBSmem = ((size_t)kBElems * 2 + 15) / 16 * 16 + 16;
 constexpr uint32_t kBCols = 512;               // whole TMEM: 4 warps per lane quadrant x 128
 
+// padded element index: non-decreasing pad (so the map is injective); the
+// pass-2 accesses of a warp fall into 16 distinct banks
 __host__ __device__ constexpr int bf_pad(int u) {
-    return u + 2 * (((u >> 8) & 15) + 7 * (u >> 12));
+    return u + 2 * ((u >> 8) + 7 * (u >> 12));
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {

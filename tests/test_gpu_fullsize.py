@@ -71,9 +71,14 @@ def test_precision_workload_16384(cmm, prec, tol):
     A64 = A.double().cpu().numpy()
     B64 = B.double().cpu().numpy()
     g = np.random.default_rng(3)
-    for r, w in [(0, int(g.integers(1 << L))), (6, int(g.integers(1 << L)))]:
+    rms = float(np.sqrt(np.mean(Rn ** 2)))
+    for r, w in [(0, int(g.integers(1 << L))), (6, int(g.integers(1 << L))),
+                 (3, int(g.integers(1 << L)))]:
         want = orc.R_entry(A64, B64, h.params, L, r, w)
         assert abs(Rn[r, w] - want) <= tol * scale, (prec, r, w, Rn[r, w], want)
+        # well inside the spread of R as well (catches a wrong transform that the
+        # norm-relative tolerance alone would let through)
+        assert abs(Rn[r, w] - want) <= 0.05 * rms, (prec, r, w, Rn[r, w], want, rms)
     # the 1024 planted entries (|S| up to a few hundred) are recovered within the noise
     si, sj = np.nonzero(S)
     est = C[torch.from_numpy(si).cuda(), torch.from_numpy(sj).cuda()].cpu().numpy()
