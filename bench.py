@@ -50,11 +50,15 @@ def parse():
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--log2b", type=int, default=16)
     ap.add_argument("--d", type=int, default=9)
-    ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--prec", default="f32", choices=["f32", "f64", "bf16tc"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--workload", default="planted",
+                    choices=["planted", "batched", "precision", "diff"],
+                    help="planted (the headline line) or one of the other configurations")
+    ap.add_argument("--tune-budget", type=float, default=120.0)
     return ap.parse_args()
 
 
@@ -362,10 +366,150 @@ def run_cmm(a):
     return 0
 
 
+def _events_ms(fn, reps):
+    import torch
+    s = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def run_batched(a):
+    """256 uneven problems in one persistent launch, replayed from a CUDA graph;
+    default tiles vs autotuned tiles."""
+    import torch
+    from paper_2601_09477_gb300 import autotune, cmm
+    from paper_2601_09477_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    d = 5
+    raw = wl.batch_problems_device(count=256, seed=1004, device="cuda")
+    probs = [cmm.Problem(At, B, cmm.make_hashes(7000 + q, d, L)) for q, (At, B, L, _) in enumerate(raw)]
+    out = {}
+    for label in ("default", "tuned"):
+        if label == "tuned":
+            for pb in probs:
+                pb.R = pb.C = None
+            t0 = time.time()
+            autotune.tune_batch(probs, d=d, cache_path=os.path.join(tempfile.gettempdir(),
+                                                                    "cmm_tune_bench.json"),
+                                budget_s=a.tune_budget)
+            out["tune_seconds"] = round(time.time() - t0, 1)
+        batch = cmm.Batch(probs, d=d)
+        for _ in range(a.warmup):
+            batch.launch()
+        assert batch.status() == cmm.OK
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            batch.launch()
+        ms = _events_ms(g.replay, a.steps)
+        assert batch.status() == cmm.OK
+        out[label + "_ms"] = round(ms, 3)
+    flops = sum(d * pb.At.shape[0] * (2.0 * (1 << pb.hashes.log2b) * pb.hashes.log2b +
+                                      (1 << pb.hashes.log2b)) for pb in probs)
+    outputs = sum(pb.At.shape[1] * pb.B.shape[1] for pb in probs)
+    best = min(out["default_ms"], out["tuned_ms"])
+    res = {"metric": "batched: 256 uneven problems (sketch + FP64 finish + median extraction), "
+                     "one persistent launch replayed from a CUDA graph, ms",
+           "value": best, "unit": "ms", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+           "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "256 problems, m,k,p uniform in [512,4096], b=2^10..2^15, d=5, "
+                                  "16 planted spikes each, FP32, A given as A^T"},
+           "alu_tops": round(flops / (best * 1e-3) / 1e12, 3), "entries_estimated": outputs,
+           "gpu_launches_per_step": 1}
+    res.update(out)
+    print(json.dumps(res), flush=True)
+    return 0
+
+
+def run_precision(a):
+    """n=16384, b=2^18, d=7: FP32 and BF16 tensor-core butterflies (and one
+    plain FP64 step) on the same input; errors of R against the FP64 form."""
+    import torch
+    from paper_2601_09477_gb300 import cmm
+    from paper_2601_09477_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    n, L, d = 16384, 18, 7
+    A, B, S = wl.orthogonal_precision(n=n, seed=1003, device="cuda")
+    h = cmm.make_hashes(2003, d, L)
+    ws = torch.empty(max(cmm.multiply_workspace_bytes(n, n, n, h, torch.float32, p)
+                         for p in ("f32", "bf16tc", "f64")), dtype=torch.uint8, device="cuda")
+    C = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    Rs, times = {}, {}
+    for prec, reps in (("f64", 1), ("f32", a.steps), ("bf16tc", a.steps)):
+        R = torch.empty((d, 1 << L), dtype=torch.float64, device="cuda")
+        fn = lambda: cmm.multiply(A, B, h, prec=prec, R=R, out=C, ws=ws)
+        for _ in range(1 if prec == "f64" else a.warmup):
+            fn()
+        times[prec] = round(_events_ms(fn, reps), 3)
+        Rs[prec] = R
+    scale = float((torch.linalg.vector_norm(A.double(), dim=0) *
+                   torch.linalg.vector_norm(B.double(), dim=1)).sum().item())
+    err = {p: float((Rs[p] - Rs["f64"]).abs().max().item() / scale) for p in ("f32", "bf16tc")}
+    rms = float(Rs["f64"].pow(2).mean().sqrt().item())
+    res = {"metric": "precision workload: multiply ms per precision, R error vs the FP64 form",
+           "value": times["bf16tc"], "unit": "ms", "n_gpus": 1, "steps": a.steps,
+           "warmup": a.warmup, "higher_is_better": False, "dtype": "bf16tc", "data": "synthetic",
+           "config": {"workload": "n=16384, A=Q orthogonal, B=Q^T S + 1e-3 noise, 1024 entries "
+                                  "N(0,1)*100, b=2^18, d=7, FP32 storage"},
+           "ms": times, "R_err_rel_to_sum_norms": err,
+           "R_err_rel_to_rms": {p: float((Rs[p] - Rs["f64"]).abs().max().item() / rms)
+                                for p in ("f32", "bf16tc")},
+           "speedup_vs_fp64": {p: round(times["f64"] / times[p], 2) for p in ("f32", "bf16tc")}}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
+def run_diff(a):
+    """n=4096 differentiable mean estimator: forward (sketch + mean at 4096
+    pairs) and backward (adjoint kernel) through the autograd Function."""
+    import torch
+    from paper_2601_09477_gb300 import cmm
+    from paper_2601_09477_gb300 import workloads as wl
+    from paper_2601_09477_gb300.autograd_fn import compressed_mean_at_pairs
+    torch.cuda.set_device(0)
+    A, B, I, J, W = wl.diff_problem(n=4096, spikes=256, pairs=4096, seed=1005)
+    h = cmm.make_hashes(2005, 5, 14)
+    Ad = torch.from_numpy(A).cuda().requires_grad_()
+    Bd = torch.from_numpy(B).cuda().requires_grad_()
+    It, Jt, Wt = (torch.from_numpy(x).cuda() for x in (I, J, W))
+
+    def fwd():
+        return compressed_mean_at_pairs(Ad, Bd, It, Jt, h, "f32")
+
+    def fwd_bwd():
+        Ad.grad = Bd.grad = None
+        (fwd().double() * Wt).sum().backward()
+
+    for _ in range(a.warmup):
+        fwd_bwd()
+    with torch.no_grad():
+        f_ms = _events_ms(fwd, a.steps)
+    fb_ms = _events_ms(fwd_bwd, a.steps)
+    res = {"metric": "differentiation: forward and forward+backward ms (mean estimator, autograd)",
+           "value": round(fb_ms, 3), "unit": "ms", "n_gpus": 1, "steps": a.steps,
+           "warmup": a.warmup, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "n=4096 FP32, N(0,1)/sqrt(n) + 256 spikes, b=2^14, d=5, "
+                                  "loss over 4096 weighted pairs"},
+           "forward_ms": round(f_ms, 3), "forward_backward_ms": round(fb_ms, 3)}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload == "batched":
+        return run_batched(a)
+    if a.workload == "precision":
+        return run_precision(a)
+    if a.workload == "diff":
+        return run_diff(a)
     return run_cmm(a)
 
 

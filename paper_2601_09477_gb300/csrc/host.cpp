@@ -275,7 +275,8 @@ int run_sketch(const void *A, int64_t lda, int transA, const void *B, int64_t ld
     double *partial = reinterpret_cast<double *>(base + pl.off_partial);
     double *Z = reinterpret_cast<double *>(base + pl.off_Z);
     {
-        Span sp(prec == CMM_PREC_F64 ? "sketch_f64" : "sketch_f32", s);
+        Span sp(prec == CMM_PREC_F64 ? "sketch_f64"
+                : prec == CMM_PREC_BF16TC ? "sketch_bf16tc" : "sketch_f32", s);
         const tab_t *tabA = reinterpret_cast<const tab_t *>(base + pl.off_tab);
         const tab_t *tabB = tabA + (size_t)hs->d * pl.C * m;
         if (prec == CMM_PREC_F64)

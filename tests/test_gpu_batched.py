@@ -103,6 +103,24 @@ def test_batched_wait_timeout_is_reported(cmm):
     _check(cmm, probs, host)
 
 
+def test_autotuner_choices_are_valid_and_correct(cmm, tmp_path):
+    from paper_2601_09477_gb300 import autotune
+    probs, host = _small_batch(cmm, seed=21)
+    cache = str(tmp_path / "tune.json")
+    tuner = autotune.tune_batch(probs, d=5, cache_path=cache, budget_s=60)
+    assert len(tuner.table) >= 3
+    for key, (tile, tt) in tuner.table.items():
+        L = int(key.split("_")[0][1:])
+        assert tt >= 0 and (tile == 0 or 5 <= tile <= min(14, L))
+    # a fresh tuner reads the cache back; the tuned batch is still exact
+    again = autotune.Tuner(cache)
+    assert again.table == tuner.table
+    batch = cmm.Batch(probs, d=5)
+    batch.launch()
+    assert batch.status() == cmm.OK
+    _check(cmm, probs, host)
+
+
 def test_batched_rejects_bad_problems(cmm):
     h = cmm.make_hashes(1, 5, 10)
     At = torch.zeros((10, 20), dtype=torch.float64, device="cuda")
