@@ -59,6 +59,49 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, float (&x)[16]) {
     for (int e = 0; e < 16; ++e) x[e] = __uint_as_float(r[e]);
 }
 
+// two 16-column loads (x and z) under one wait
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ax, float (&x)[16], uint32_t az, float (&z)[16]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%33];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(ax), "r"(az)
+        : "memory");
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        x[e] = __uint_as_float(r[e]);
+        z[e] = __uint_as_float(r[16 + e]);
+    }
+}
+
+// store without waiting; tmem_wait_st() before the columns are read again or
+// the source registers are overwritten by a later st
+__device__ __forceinline__ void tmem_st16_nowait(uint32_t addr, const float *x) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+        :
+        : "r"(addr), "r"(__float_as_uint(x[0])), "r"(__float_as_uint(x[1])),
+          "r"(__float_as_uint(x[2])), "r"(__float_as_uint(x[3])), "r"(__float_as_uint(x[4])),
+          "r"(__float_as_uint(x[5])), "r"(__float_as_uint(x[6])), "r"(__float_as_uint(x[7])),
+          "r"(__float_as_uint(x[8])), "r"(__float_as_uint(x[9])), "r"(__float_as_uint(x[10])),
+          "r"(__float_as_uint(x[11])), "r"(__float_as_uint(x[12])), "r"(__float_as_uint(x[13])),
+          "r"(__float_as_uint(x[14])), "r"(__float_as_uint(x[15]))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tmem_st16(uint32_t addr, const float *x) {
     asm volatile(
         "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
@@ -147,20 +190,22 @@ sketch_tm_kernel(const float *__restrict__ At, int64_t ldat, const float *__rest
 
     float v[kTmE];
     for (int64_t t = t0; t < t1; ++t) {
-        scatter_table<float, kTmL, kTmLE, 16>(S, At + t * ldat, tA, m, q);
+        // all of a thread's column values are loaded before its atomics
+        // (the registers of v are free during the scatter)
+        scatter_table<float, kTmL, kTmLE, 32>(S, At + t * ldat, tA, m, q);
         __syncthreads();
         tm_fwht(S, v, q);
 #pragma unroll
-        for (int c = 0; c < kTmE / 16; ++c) tmem_st16(tx + 16 * c, v + 16 * c);
+        for (int c = 0; c < kTmE / 16; ++c) tmem_st16_nowait(tx + 16 * c, v + 16 * c);
+        tmem_wait_st();
         __syncthreads();
-        scatter_table<float, kTmL, kTmLE, 16>(S, Bp + t * ldbp, tB, p, q);
+        scatter_table<float, kTmL, kTmLE, 32>(S, Bp + t * ldbp, tB, p, q);
         __syncthreads();
         tm_fwht(S, v, q);
 #pragma unroll
         for (int c = 0; c < kTmE / 16; ++c) {
             float xs[16], zs[16];
-            tmem_ld16(tx + 16 * c, xs);
-            tmem_ld16(tz + 16 * c, zs);
+            tmem_ld16x2(tx + 16 * c, xs, tz + 16 * c, zs);
 #pragma unroll
             for (int e = 0; e < 16; e += 2) {
                 const float2 acc = __ffma2_rn(make_float2(xs[e], xs[e + 1]),
@@ -169,8 +214,9 @@ sketch_tm_kernel(const float *__restrict__ At, int64_t ldat, const float *__rest
                 zs[e] = acc.x;
                 zs[e + 1] = acc.y;
             }
-            tmem_st16(tz + 16 * c, zs);
+            tmem_st16_nowait(tz + 16 * c, zs);
         }
+        tmem_wait_st();
         __syncthreads();
     }
 
