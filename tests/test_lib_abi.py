@@ -104,3 +104,25 @@ def test_workspace_queries_scale(cmm):
     assert lib.cmm_extract_workspace_bytes(100, 100, 5) >= 5 * 200 * 4
     assert lib.cmm_multiply_workspace_bytes(256, 256, 256, 5, 12, cmm.F64, cmm.PREC_F64, 0) >= \
         5 * 4096 * 8
+
+
+def test_parameter_rule_and_categories():
+    # d = 2 floor(c_d log2 n / 2) + 1, b = c_b n (Sec. 5.6)
+    import importlib
+    ev = importlib.import_module("paper_2601_09477_gb300.evaluate")
+    assert ev.params(1024, 1.0, 0.5) == (11, 9)
+    assert ev.params(2 ** 15, 0.25, 0.25) == (3, 13)     # formula, not "next odd >= c_d log2 n"
+    assert ev.params(2 ** 17, 2.0, 4.0) == (35, 19)
+    n = 1024
+    base = {"big": 10, "small": n * n - 10}
+    perfect = dict(base, **{"B_ge_0.5": 10, "S_le_0.5": n * n - 10, "B_eps_le_0.1": 10,
+                            "S_eps_le_0.1": n * n - 10})
+    assert ev.category(perfect, n) == "perfect"
+    good = dict(perfect, **{"S_eps_le_0.1": n * n - 10 - n})
+    assert ev.category(good, n) == "good"
+    decent = dict(good, **{"B_eps_le_0.1": 1, "S_eps_le_0.1": int(0.995 * (n * n - 10))})
+    assert ev.category(decent, n) == "decent"
+    sat = dict(decent, **{"B_eps_le_0.1": 0})
+    assert ev.category(sat, n) == "satisfactory"
+    none = dict(sat, **{"B_ge_0.5": 5})
+    assert ev.category(none, n) == "none"
