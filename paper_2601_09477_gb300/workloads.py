@@ -192,8 +192,10 @@ def diff_problem(n: int = 4096, spikes: int = 256, pairs: int = 4096, seed: int 
 
 def logunit(n: int, seed: int = 2001):
     """C = D P: log2 n entries equal to 1, the rest 0.001, one per row/column.
-    A = A~ D1, B = A~^{-1} D2 P with floor(log2 n / 2) (resp. ceil) entries 100
-    and the rest 0.01 on D1 (resp. D2, on disjoint positions)."""
+    A = D1 A~, B = A~^{-1} D2 P with floor(log2 n / 2) (resp. ceil) entries 100
+    and the rest 0.01 on D1 (resp. D2, on disjoint positions).  (The paper
+    writes A = A~ D1 but derives A B = D1 A~ A~^{-1} D2 P = D1 D2 P, which needs
+    D1 on the left.)"""
     g = rng(seed)
     L = int(math.log2(n))
     At = g.uniform(-1.0, 1.0, size=(n, n))
@@ -205,7 +207,7 @@ def logunit(n: int, seed: int = 2001):
     perm = g.permutation(n)
     P = np.zeros((n, n))
     P[np.arange(n), perm] = 1.0
-    A = At * d1[None, :]
+    A = d1[:, None] * At
     B = np.linalg.solve(At, np.diag(d2) @ P)
     C = (d1 * d2)[:, None] * P
     return np.ascontiguousarray(A), np.ascontiguousarray(B), C
