@@ -267,7 +267,7 @@ def run_cmm(a):
     sk_name = "sketch_" + a.prec
     launches = sum(v[0] for v in trace.values())
     sk_launches, sk_ms_total = trace.get(sk_name, (0, 0.0))
-    sk_ms = sk_ms_total / max(sk_launches, 1)
+    sk_ms = sk_ms_total / a.steps   # one sketch call per step
     b = 1 << L
     ops = d * n * (2.0 * b * L + b)   # butterfly add/sub of both sketches + one FMA per bucket
     hbm_gbs, hbm_kind, pk = peaks()

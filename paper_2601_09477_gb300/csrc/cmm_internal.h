@@ -42,7 +42,7 @@ struct SketchPlan {
     int threads;           // CTA size
     size_t smem;           // dynamic shared memory per CTA
     // workspace carve-up (byte offsets into ws)
-    size_t off_At, off_Bp, off_partial, off_Z, off_tab, total;
+    size_t off_At, off_Bp, off_partial, off_Z, off_tab, off_colmax, total;
     bool prep_A, prep_B;   // whether A / B are converted into the workspace
     int64_t ldat, ldbp;    // leading dimensions of the operands the sketch reads
     bool tmem;             // use the TMEM variant of the FP32 kernel
@@ -79,6 +79,10 @@ cudaError_t launch_prep_A(const void *A, int64_t lda, int transA, int dtype, int
                           int64_t m, int64_t k, void *At, int64_t ldat, cudaStream_t s);
 cudaError_t launch_prep_B(const void *B, int64_t ldb, int dtype, int prec,
                           int64_t k, int64_t p, void *Bp, int64_t ldbp, cudaStream_t s);
+// out[r] = max_c |X[r][c]| over the rows x cols FP32 array X (leading dimension
+// ldx): the per-column scale of the fixed-point scatter
+cudaError_t launch_rowmax(const float *X, int64_t ldx, int64_t rows, int64_t cols, float *out,
+                          cudaStream_t s);
 // tabA / tabB: scatter tables (d * C * m and d * C * p words, built by the
 // launcher when not null)
 cudaError_t launch_sketch_f32(const SketchPlan &pl, const float *At, const float *Bp,
@@ -95,10 +99,14 @@ cudaError_t launch_finish(const double *partial, int nchunks, int d, int L, doub
 bool sketch_tm_supported(int prec, int Llo);
 int sketch_tm_threads();
 size_t sketch_tm_smem();
+// scatter tables of the TMEM kernel (d * C * m and d * C * p words)
+cudaError_t launch_sketch_tm_tables(const SketchPlan &pl, int64_t m, int64_t p, int d,
+                                    const HashParams &hp, tab_t *tabA, tab_t *tabB,
+                                    cudaStream_t s);
+// colmax: max |A[i][t]| over i for each t, then max |B[t][j]| over j (2k floats)
 cudaError_t launch_sketch_tm(const SketchPlan &pl, const float *At, const float *Bp, int64_t m,
-                             int64_t k, int64_t p, int d, const HashParams &hp,
-                             const tab_t *tabA, const tab_t *tabB, double *partial,
-                             cudaStream_t s);
+                             int64_t k, int64_t p, int d, const tab_t *tabA, const tab_t *tabB,
+                             const float *colmax, double *partial, cudaStream_t s);
 // BF16 tensor-core variant (2^15-point slices, 32-bit scatter tables)
 int sketch_bf16_llo();
 int sketch_bf16_threads();

@@ -55,6 +55,29 @@ __global__ void __launch_bounds__(256) convert_kernel(const TI *__restrict__ X, 
     }
 }
 
+// out[r] = max_c |X[r][c]| (0 for an empty row): one CTA of 256 threads per row
+__global__ void __launch_bounds__(256) rowmax_kernel(const float *__restrict__ X, int64_t ldx,
+                                                     int64_t rows, int64_t cols,
+                                                     float *__restrict__ out) {
+    __shared__ float red[8];
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const float *row = X + r * ldx;
+        float mx = 0.f;
+        for (int64_t c = threadIdx.x; c < cols; c += 256) mx = fmaxf(mx, fabsf(__ldcs(row + c)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float m = red[0];
+#pragma unroll
+            for (int w = 1; w < 8; ++w) m = fmaxf(m, red[w]);
+            out[r] = m;
+        }
+        __syncthreads();
+    }
+}
+
 unsigned grid_for(int64_t work, int64_t per_block) {
     int64_t g = (work + per_block - 1) / per_block;
     if (g > 152 * 32) g = 152 * 32;
@@ -125,6 +148,14 @@ cudaError_t launch_convert_out(const void *src, int src_f64, int64_t rows, int64
     else if (!src_f64 && dst_dtype == CMM_F32) { CMM_CONV(float, float) }
     else return cudaErrorInvalidValue;
 #undef CMM_CONV
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rowmax(const float *X, int64_t ldx, int64_t rows, int64_t cols, float *out,
+                          cudaStream_t s) {
+    if (rows <= 0) return cudaSuccess;
+    const int64_t g = rows < 152 * 16 ? rows : 152 * 16;
+    rowmax_kernel<<<(unsigned)g, 256, 0, s>>>(X, ldx, rows, cols, out);
     return cudaGetLastError();
 }
 

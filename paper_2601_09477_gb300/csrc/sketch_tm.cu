@@ -14,6 +14,17 @@
 // each with its own barriers, so one CTA's scatter overlaps the other's
 // butterflies.
 //
+// Scatter in fixed point.  Shared-memory FP32 atomic adds are far slower than
+// integer ones on this GPU, so each column is scattered as 32-bit integers:
+// value a becomes round(a * 2^e), with one power of two 2^e per (CTA, column)
+// chosen so that c_max * max_i |a_i| * 2^e < 2^30, c_max being the largest
+// number of elements that share a bucket in this CTA's table.  Every bucket
+// sum is then an exact integer below 2^31 (no overflow, no dependence on the
+// order of the atomics), and it is rounded once to FP32 and scaled back by
+// 2^-e when the first register round reads it.  The only error beyond FP32's
+// is the quantisation of each value to a multiple of 2^-e, at most
+// c_max * max|a| * 2^-30; integer-valued inputs (+-1) stay exact.
+//
 // Layout of the slice in shared memory: element u at word u + 4 * (u >> 7).
 // Round 0: thread q holds u = 128 q + j (a contiguous, 16-byte aligned row of
 // 128 words, read and written as float4); round 1: u = q + 128 j (the 32
@@ -34,11 +45,11 @@ constexpr int kTmStride = (1 << kTmL) + 4 * ((1 << kTmL) >> kTmLE);
 // shared memory: the slice plus the TMEM address word.  Registers (about 250
 // per thread) hold the SM to two CTAs, matching the 2 x 256 TMEM columns; the
 // rest of the unified L1 caches the scatter tables.
-constexpr size_t kTmSmem = kTmStride * sizeof(float) + 16;
+constexpr size_t kTmSmem = kTmStride * sizeof(float) + 32;
 constexpr uint32_t kTmCols = 256;          // 128 columns H x_t + 128 columns Z per lane
 
 static_assert(kTmP == 128, "one TMEM lane per thread");
-static_assert(kTmStride * 4 + 16 <= (int)kTmSmem, "slice must fit");
+static_assert(kTmStride * 4 + 32 <= (int)kTmSmem, "slice, TMEM address and reduction words must fit");
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -118,16 +129,21 @@ __device__ __forceinline__ void tmem_st16(uint32_t addr, const float *x) {
 }
 
 // the 2^14-point FWHT of the slice S in two register rounds; result in v
-// with v[j] = element q + 128 j; the slice is left zeroed
-__device__ __forceinline__ void tm_fwht(float *S, float (&v)[kTmE], int q) {
+// with v[j] = element q + 128 j; the slice is left zeroed.  On entry S holds
+// the integer bucket sums of the fixed-point scatter, scaled back by inv.
+__device__ __forceinline__ void tm_fwht(float *S, float (&v)[kTmE], int q, float inv) {
     float4 *row = reinterpret_cast<float4 *>(S + 132 * q);
+    const int4 *irow = reinterpret_cast<const int4 *>(row);
+    const float2 inv2 = make_float2(inv, inv);
 #pragma unroll
     for (int c = 0; c < kTmE / 4; ++c) {
-        const float4 w = row[c];
-        v[4 * c] = w.x;
-        v[4 * c + 1] = w.y;
-        v[4 * c + 2] = w.z;
-        v[4 * c + 3] = w.w;
+        const int4 w = irow[c];
+        const float2 lo = __fmul2_rn(make_float2(__int2float_rn(w.x), __int2float_rn(w.y)), inv2);
+        const float2 hi = __fmul2_rn(make_float2(__int2float_rn(w.z), __int2float_rn(w.w)), inv2);
+        v[4 * c] = lo.x;
+        v[4 * c + 1] = lo.y;
+        v[4 * c + 2] = hi.x;
+        v[4 * c + 3] = hi.y;
     }
     reg_fwht_f32<kTmE, kTmLE>(v);
 #pragma unroll
@@ -141,14 +157,74 @@ __device__ __forceinline__ void tm_fwht(float *S, float (&v)[kTmE], int q) {
     for (int j = 0; j < kTmE; ++j) S[q + 132 * j] = 0.f;
 }
 
+// largest number of table entries that share a bucket (the slice Si must be
+// zero on entry; it is zero again on return); all threads of the CTA
+__device__ __forceinline__ int table_cmax(int *Si, const tab_t *__restrict__ tab, int64_t n,
+                                          int q, int *red) {
+    for (int64_t i = q; i < n; i += kTmP) atomicAdd(Si + (__ldg(tab + i) & 0x7fffu), 1);
+    __syncthreads();
+    int mx = 0;
+    for (int i = q; i < kTmStride; i += kTmP) {
+        mx = max(mx, Si[i]);
+        Si[i] = 0;
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((q & 31) == 0) red[q >> 5] = mx;
+    __syncthreads();
+    mx = max(max(red[0], red[1]), max(red[2], red[3]));
+    __syncthreads();
+    return mx;
+}
+
+// the power of two 2^e of one column: cmax * colmax * 2^e < 2^30, with e kept
+// in [-126, 126] so that 2^e and 2^-e are normal floats
+__device__ __forceinline__ void fixed_scale(float colmax, int cmax, float &s, float &inv) {
+    // colmax < 2^Ec (exponent field - 126; 0 and subnormals give -126) and
+    // cmax < 2^Ek, so the product is below 2^(Ec + Ek)
+    const int Ec = ((__float_as_int(colmax) >> 23) & 0xff) - 126;
+    const int Ek = 32 - __clz(cmax);
+    const int e = min(max(30 - Ec - Ek, -126), 126);
+    s = __int_as_float((127 + e) << 23);
+    inv = __int_as_float((127 - e) << 23);
+}
+
+// scatter one column as integers round(a * s) with the packed table
+template <int B>
+__device__ __forceinline__ void scatter_fixed(int *Si, const float *__restrict__ col,
+                                              const tab_t *__restrict__ tab, int64_t n, int q,
+                                              float s) {
+    int64_t i = q;
+    for (; i + (B - 1) * (int64_t)kTmP < n; i += B * (int64_t)kTmP) {
+        float val[B];
+        tab_t w[B];
+#pragma unroll
+        for (int e = 0; e < B; ++e) {
+            val[e] = ld_stream(col + i + e * (int64_t)kTmP);
+            w[e] = __ldg(tab + i + e * (int64_t)kTmP);
+        }
+#pragma unroll
+        for (int e = 0; e < B; ++e) {
+            const int iv = __float2int_rn(val[e] * s);
+            atomicAdd(Si + (w[e] & 0x7fffu), (w[e] >> 15) ? -iv : iv);
+        }
+    }
+    for (; i < n; i += kTmP) {
+        const tab_t w = __ldg(tab + i);
+        const int iv = __float2int_rn(ld_stream(col + i) * s);
+        atomicAdd(Si + (w & 0x7fffu), (w >> 15) ? -iv : iv);
+    }
+}
+
 __global__ void __launch_bounds__(kTmP, 2)
 sketch_tm_kernel(const float *__restrict__ At, int64_t ldat, const float *__restrict__ Bp,
                  int64_t ldbp, int64_t m, int64_t k, int64_t p, int Lfull, int C, int64_t chunk,
                  int d, const tab_t *__restrict__ tabA, const tab_t *__restrict__ tabB,
-                 double *__restrict__ partial) {
+                 const float *__restrict__ colmax, double *__restrict__ partial) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *S = reinterpret_cast<float *>(smem_raw);
+    int *Si = reinterpret_cast<int *>(smem_raw);
     uint32_t *s_taddr = reinterpret_cast<uint32_t *>(smem_raw + kTmStride * sizeof(float));
+    int *s_red = reinterpret_cast<int *>(smem_raw + kTmStride * sizeof(float) + 16);
     const int q = threadIdx.x;
     const int warp = q >> 5;
 
@@ -178,6 +254,8 @@ sketch_tm_kernel(const float *__restrict__ At, int64_t ldat, const float *__rest
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // this warp's lanes: 32 * warp .. 32 * warp + 31; columns [0,128) H x, [128,256) Z
+    const int cmaxA = table_cmax(Si, tA, m, q, s_red);
+    const int cmaxB = table_cmax(Si, tB, p, q, s_red);
     const uint32_t tx = *s_taddr + ((uint32_t)(32 * warp) << 16);
     const uint32_t tz = tx + 128;
     {
@@ -192,16 +270,19 @@ sketch_tm_kernel(const float *__restrict__ At, int64_t ldat, const float *__rest
     for (int64_t t = t0; t < t1; ++t) {
         // all of a thread's column values are loaded before its atomics
         // (the registers of v are free during the scatter)
-        scatter_table<float, kTmL, kTmLE, 32>(S, At + t * ldat, tA, m, q);
+        float sA, invA, sB, invB;
+        fixed_scale(__ldg(colmax + t), cmaxA, sA, invA);
+        fixed_scale(__ldg(colmax + k + t), cmaxB, sB, invB);
+        scatter_fixed<32>(Si, At + t * ldat, tA, m, q, sA);
         __syncthreads();
-        tm_fwht(S, v, q);
+        tm_fwht(S, v, q, invA);
 #pragma unroll
         for (int c = 0; c < kTmE / 16; ++c) tmem_st16_nowait(tx + 16 * c, v + 16 * c);
         tmem_wait_st();
         __syncthreads();
-        scatter_table<float, kTmL, kTmLE, 32>(S, Bp + t * ldbp, tB, p, q);
+        scatter_fixed<32>(Si, Bp + t * ldbp, tB, p, q, sB);
         __syncthreads();
-        tm_fwht(S, v, q);
+        tm_fwht(S, v, q, invB);
 #pragma unroll
         for (int c = 0; c < kTmE / 16; ++c) {
             float xs[16], zs[16];
@@ -244,25 +325,28 @@ bool sketch_tm_supported(int prec, int Llo) { return prec == CMM_PREC_F32 && Llo
 int sketch_tm_threads() { return kTmP; }
 size_t sketch_tm_smem() { return kTmSmem; }
 
-cudaError_t launch_sketch_tm(const SketchPlan &pl, const float *At, const float *Bp, int64_t m,
-                             int64_t k, int64_t p, int d, const HashParams &hp,
-                             const tab_t *tabA, const tab_t *tabB, double *partial,
-                             cudaStream_t s) {
+cudaError_t launch_sketch_tm_tables(const SketchPlan &pl, int64_t m, int64_t p, int d,
+                                    const HashParams &hp, tab_t *tabA, tab_t *tabB,
+                                    cudaStream_t s) {
     const int64_t n = (int64_t)d * pl.C * (m + p);
     int64_t g = (n + 255) / 256;
     if (g > 152 * 32) g = 152 * 32;
     if (g < 1) g = 1;
-    sketch_table_kernel<float, kTmL, kTmLE><<<(unsigned)g, 256, 0, s>>>(
-        hp, d, pl.L, kTmL, pl.C, m, p, const_cast<tab_t *>(tabA), const_cast<tab_t *>(tabB));
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(sketch_tm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kTmSmem);
+    sketch_table_kernel<float, kTmL, kTmLE><<<(unsigned)g, 256, 0, s>>>(hp, d, pl.L, kTmL, pl.C,
+                                                                     m, p, tabA, tabB);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_tm(const SketchPlan &pl, const float *At, const float *Bp, int64_t m,
+                             int64_t k, int64_t p, int d, const tab_t *tabA, const tab_t *tabB,
+                             const float *colmax, double *partial, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(sketch_tm_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmSmem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (int64_t)pl.nchunks * d * pl.C;
     sketch_tm_kernel<<<(unsigned)blocks, kTmP, kTmSmem, s>>>(At, pl.ldat, Bp, pl.ldbp, m, k, p,
                                                              pl.L, pl.C, pl.chunk, d, tabA, tabB,
-                                                             partial);
+                                                             colmax, partial);
     return cudaGetLastError();
 }
 
