@@ -7,11 +7,17 @@
 // the FP64 finish (one task per (q, r): reduction over blocks, inverse
 // transform, 1/b), and Decompress of every entry (one task per tile of rows).
 //
-// The task list is ordered sketch tasks of all problems, then finish tasks,
-// then extraction tasks.  CTAs (one per SM) take tasks from an atomic
-// counter.  A finish task waits until all sketch tasks of its (q, r) are done
-// and an extraction task until all d finish tasks of q are done; both waits
-// are bounded (a clock64 budget): on expiry the kernel sets an error word,
+// The sketch scatters in fixed point (one power-of-two scale per column, see
+// sketch_impl.cuh), which needs the maxima |A^T[t][:]| and |B[t][:]| of every
+// column first: column-maximum tasks (rows of A^T and B in blocks) come first
+// in the task list.
+//
+// The task list is ordered column-maximum tasks, sketch tasks of all problems,
+// then finish tasks, then extraction tasks.  CTAs (one per SM) take tasks from
+// an atomic counter.  A sketch task waits until the column maxima of its
+// problem are done, a finish task until all sketch tasks of its (q, r) are
+// done and an extraction task until all d finish tasks of q are done; the waits
+// are bounded (a globaltimer budget): on expiry the kernel sets an error word,
 // every CTA stops taking tasks, and cmm_batched_status returns
 // CMM_ERR_TIMEOUT.  Because every task is dequeued after all tasks it depends
 // on and sketch tasks wait on nothing, the waits always end in a correct run.
@@ -38,6 +44,7 @@ constexpr int kBMaxLlo = 14;
 constexpr int kBFinishLf = 12;
 constexpr size_t kBSmem = 160 * 1024;
 constexpr int kExTileRows = 32;
+constexpr int kCmRows = 64;   // rows of A^T / B per column-maximum task
 constexpr unsigned long long kDefaultWaitNs = 4000000000ULL;   // 4 s
 
 struct BProblem {
@@ -50,20 +57,23 @@ struct BProblem {
     int64_t chunk;
     double *partial, *Z, *R, *Cout;
     int64_t ldc;
+    float *cm;      // column maxima: A^T rows [0, k), then B rows [k, 2k)
     int hash_off;
     int ex_tiles;
+    int cm_tasks;
 };
 
 struct BTask {
-    int32_t type;   // 0 sketch, 1 finish, 2 extract
+    int32_t type;   // 0 sketch, 1 finish, 2 extract, 3 column maxima
     int32_t prob;
-    int32_t a;      // sketch: r * C + u_hi; finish: r; extract: row tile
+    int32_t a;      // sketch: r * C + u_hi; finish: r; extract: row tile; maxima: row block
     int32_t b;      // sketch: block of inner indices
 };
 
-// counters: [0] next task, [1] error word, then done_sketch[Q * d], done_finish[Q]
+// counters: [0] next task, [1] error word, then done_sketch[Q * d],
+// done_finish[Q], done_cm[Q]
 struct BCounters {
-    int *next, *err, *done_sketch, *done_finish;
+    int *next, *err, *done_sketch, *done_finish, *done_cm;
 };
 
 __device__ __forceinline__ int load_acquire(const int *p) {
@@ -120,7 +130,25 @@ __device__ __forceinline__ void sketch_task(const BProblem &pr, const HashRep &H
     const int64_t b = (int64_t)1 << pr.L;
     double *out = pr.partial + ((int64_t)blk * d + r) * b + (int64_t)u_hi * (1 << L);
     sketch_block<float, float, L, LE, kBThreads>(pr.At, pr.ldat, pr.Bp, pr.ldbp, pr.m, pr.p, pr.L,
-                                                 u_hi, t0, t1, H, nullptr, nullptr, out, smem);
+                                                 u_hi, t0, t1, H, nullptr, nullptr, pr.cm,
+                                                 pr.cm + pr.k, out, smem);
+}
+
+// max |x| over rows [blk * kCmRows, ...) of A^T (rows < k) and B (rows >= k)
+__device__ void colmax_task(const BProblem &pr, int blk) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t r0 = (int64_t)blk * kCmRows;
+    const int64_t r1 = r0 + kCmRows < 2 * pr.k ? r0 + kCmRows : 2 * pr.k;
+    for (int64_t r = r0 + warp; r < r1; r += kBThreads / 32) {
+        const bool isA = r < pr.k;
+        const float *row = isA ? pr.At + r * pr.ldat : pr.Bp + (r - pr.k) * pr.ldbp;
+        const int64_t n = isA ? pr.m : pr.p;
+        float mx = 0.f;
+        for (int64_t c = lane; c < n; c += 32) mx = fmaxf(mx, fabsf(__ldcs(row + c)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) pr.cm[r] = mx;
+    }
 }
 
 __device__ void dispatch_sketch(const BProblem &pr, const HashRep &H, int a, int blk, int d,
@@ -275,7 +303,11 @@ batched_kernel(const BTask *__restrict__ tasks, int ntasks, const BProblem *__re
         if (tid >= ntasks) break;
         const BTask tk = tasks[tid];
         const BProblem &pr = probs[tk.prob];
-        if (tk.type == 0) {
+        if (tk.type == 3) {
+            colmax_task(pr, tk.a);
+            signal_done(ctr.done_cm + tk.prob);
+        } else if (tk.type == 0) {
+            if (!wait_for(ctr.done_cm + tk.prob, pr.cm_tasks, ctr.err, &s_flag, budget_ns)) break;
             const int r = tk.a / pr.C;
             dispatch_sketch(pr, hashes[pr.hash_off + r], tk.a, tk.b, d, smem_raw);
             signal_done(ctr.done_sketch + tk.prob * d + r);
@@ -324,7 +356,7 @@ int64_t default_chunk(int Llo, int64_t k) {
 struct Sizes {
     std::vector<int> Llo, C, nchunks;
     std::vector<int64_t> chunk;
-    std::vector<size_t> off_part, off_Z, off_At, off_Bp;
+    std::vector<size_t> off_part, off_Z, off_At, off_Bp, off_cm;
     size_t total;
     size_t off_ctr, ctr_bytes, off_tasks, off_probs, off_hash;
     int ntasks;
@@ -339,9 +371,10 @@ int plan_sizes(const cmm_problem *pb, int Q, int d, Sizes &sz) {
     sz.off_Z.resize(Q);
     sz.off_At.resize(Q);
     sz.off_Bp.resize(Q);
+    sz.off_cm.resize(Q);
     size_t off = 0;
     sz.off_ctr = off;
-    sz.ctr_bytes = (size_t)(2 + Q * d + Q) * sizeof(int);
+    sz.ctr_bytes = (size_t)(2 + Q * d + 2 * Q) * sizeof(int);
     off += aup(sz.ctr_bytes);
     int64_t ntasks = 0;
     for (int q = 0; q < Q; ++q) {
@@ -356,7 +389,8 @@ int plan_sizes(const cmm_problem *pb, int Q, int d, Sizes &sz) {
         sz.chunk[q] = ch;
         sz.nchunks[q] = (int)((kk + ch - 1) / ch);
         const int64_t tiles = (P.m + kExTileRows - 1) / kExTileRows;
-        ntasks += (int64_t)d * sz.C[q] * sz.nchunks[q] + d + (P.C ? tiles : 0);
+        ntasks += (int64_t)d * sz.C[q] * sz.nchunks[q] + d + (P.C ? tiles : 0) +
+                  (2 * P.k + kCmRows - 1) / kCmRows;
     }
     if (ntasks > 0x7fffffff) return -2;
     sz.ntasks = (int)ntasks;
@@ -375,6 +409,8 @@ int plan_sizes(const cmm_problem *pb, int Q, int d, Sizes &sz) {
         off += aup((size_t)sz.nchunks[q] * d * b * sizeof(double));
         sz.off_Z[q] = off;
         off += aup((size_t)d * b * sizeof(double));
+        sz.off_cm[q] = off;
+        off += aup((size_t)2 * P.k * sizeof(float));
     }
     sz.total = off;
     return 0;
@@ -455,8 +491,10 @@ extern "C" int cmm_batched_prepare(const cmm_problem *problems, int32_t Q, int32
         bp.R = P.R;
         bp.Cout = P.C;
         bp.ldc = P.ldc;
+        bp.cm = reinterpret_cast<float *>(base + sz.off_cm[q]);
         bp.hash_off = q * d;
         bp.ex_tiles = (int)((P.m + kExTileRows - 1) / kExTileRows);
+        bp.cm_tasks = (int)((2 * P.k + kCmRows - 1) / kCmRows);
         for (int r = 0; r < d; ++r) {
             const uint64_t *w = P.hash_params + 8 * r;
             hashes[(size_t)q * d + r] = HashRep{w[0], w[1], w[2], w[3], w[4], w[5], w[6], w[7]};
@@ -470,6 +508,8 @@ extern "C" int cmm_batched_prepare(const cmm_problem *problems, int32_t Q, int32
         const double wy = (double)probs[y].k * (1 << probs[y].L) * probs[y].L;
         return wx > wy;
     });
+    for (int q : order)
+        for (int c = 0; c < probs[q].cm_tasks; ++c) tasks.push_back(BTask{3, q, c, 0});
     for (int q : order)
         for (int c = 0; c < probs[q].nchunks; ++c)
             for (int a = 0; a < d * probs[q].C; ++a) tasks.push_back(BTask{0, q, a, c});
@@ -515,7 +555,7 @@ cudaError_t launch_batched_inst(const BPlan &bp, unsigned long long budget_ns, i
                                 cudaStream_t s) {
     char *base = static_cast<char *>(bp.ws);
     int *ctr = reinterpret_cast<int *>(base + bp.off_ctr);
-    BCounters c{ctr, ctr + 1, ctr + 2, ctr + 2 + bp.Q * bp.d};
+    BCounters c{ctr, ctr + 1, ctr + 2, ctr + 2 + bp.Q * bp.d, ctr + 2 + bp.Q * bp.d + bp.Q};
     auto kern = batched_kernel<D>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBSmem);
     if (e != cudaSuccess) return e;

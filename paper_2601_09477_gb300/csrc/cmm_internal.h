@@ -84,15 +84,16 @@ cudaError_t launch_prep_B(const void *B, int64_t ldb, int dtype, int prec,
 cudaError_t launch_rowmax(const float *X, int64_t ldx, int64_t rows, int64_t cols, float *out,
                           cudaStream_t s);
 // tabA / tabB: scatter tables (d * C * m and d * C * p words, built by the
-// launcher when not null)
+// launcher when not null); colmax: the 2k column maxima of the FP32
+// fixed-point scatter (A^T rows, then B rows), unused by FP64
 cudaError_t launch_sketch_f32(const SketchPlan &pl, const float *At, const float *Bp,
                               int64_t m, int64_t k, int64_t p, int d, const HashParams &hp,
-                              const tab_t *tabA, const tab_t *tabB, double *partial,
-                              cudaStream_t s);
+                              const tab_t *tabA, const tab_t *tabB, const float *colmax,
+                              double *partial, cudaStream_t s);
 cudaError_t launch_sketch_f64(const SketchPlan &pl, const double *At, const double *Bp,
                               int64_t m, int64_t k, int64_t p, int d, const HashParams &hp,
-                              const tab_t *tabA, const tab_t *tabB, double *partial,
-                              cudaStream_t s);
+                              const tab_t *tabA, const tab_t *tabB, const float *colmax,
+                              double *partial, cudaStream_t s);
 cudaError_t launch_finish(const double *partial, int nchunks, int d, int L, double *Z,
                           double *R, cudaStream_t s);
 // TMEM variant of the FP32 sketch kernel (2^14-point slices)

@@ -172,15 +172,47 @@ __device__ __forceinline__ void round_store(T *base, const T (&v)[1 << LE]) {
     }
 }
 
+// round-0 load of FP32 values from integer bucket sums (the fixed-point
+// scatter): v = float(sum) * inv, inv a power of two
+template <int L, int LE>
+__device__ __forceinline__ void round_load_fixed(const float *base, float (&v)[1 << LE],
+                                                 float inv) {
+    using RK = typename FwhtShape<float, L, LE>::template Round<0>;
+    constexpr int E = 1 << LE;
+    const int *ib = reinterpret_cast<const int *>(base);
+    if constexpr (PadOf<float, L, LE>::value == 4) {
+        const int4 *b4 = reinterpret_cast<const int4 *>(ib);
+#pragma unroll
+        for (int c = 0; c < E / 4; ++c) {
+            const int4 w = b4[c];
+            v[4 * c] = __int2float_rn(w.x) * inv;
+            v[4 * c + 1] = __int2float_rn(w.y) * inv;
+            v[4 * c + 2] = __int2float_rn(w.z) * inv;
+            v[4 * c + 3] = __int2float_rn(w.w) * inv;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < E; ++j) v[j] = __int2float_rn(ib[RK::addr(0, j)]) * inv;
+    }
+}
+
 // Transform the group's slice Sg in place, leaving the result in registers v
-// (round NR-1 layout) and the shared array zeroed for the next scatter.
-template <typename T, int L, int LE, int K>
-__device__ __forceinline__ void fwht_rounds(T *Sg, T (&v)[1 << LE], int q, int g) {
+// (round NR-1 layout) and the shared array zeroed for the next scatter.  With
+// FX (FP32 only) the slice holds the integer sums of the fixed-point scatter,
+// converted with the scale inv when round 0 reads them.
+template <typename T, int L, int LE, int K, bool FX = false>
+__device__ __forceinline__ void fwht_rounds(T *Sg, T (&v)[1 << LE], int q, int g,
+                                            float inv = 1.f) {
     using S = FwhtShape<T, L, LE>;
     using RK = typename S::template Round<K>;
     constexpr int E = S::E;
     T *base = Sg + RK::addr(q, 0);
-    round_load<T, L, LE, K>(base, v);
+    if constexpr (FX && K == 0) {
+        static_assert(sizeof(T) == 4, "fixed-point scatter is FP32 only");
+        round_load_fixed<L, LE>(base, v, inv);
+    } else {
+        round_load<T, L, LE, K>(base, v);
+    }
     reg_fwht_any<T, E, RK::nb>(v);
     if constexpr (K + 1 < S::NR) {
         round_store<T, L, LE, K>(base, v);

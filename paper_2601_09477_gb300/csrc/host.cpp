@@ -200,7 +200,7 @@ bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int p
     pl.off_tab = off;
     off += align_up((size_t)d * pl.C * (m + p) * (bf16 ? sizeof(uint32_t) : sizeof(tab_t)));
     pl.off_colmax = off;
-    if (pl.tmem) off += align_up((size_t)2 * k * sizeof(float));
+    if (prec == CMM_PREC_F32) off += align_up((size_t)2 * k * sizeof(float));
     pl.total = off;
     return true;
 }
@@ -278,21 +278,21 @@ int run_sketch(const void *A, int64_t lda, int transA, const void *B, int64_t ld
     double *Z = reinterpret_cast<double *>(base + pl.off_Z);
     const tab_t *tabA = reinterpret_cast<const tab_t *>(base + pl.off_tab);
     const tab_t *tabB = tabA + (size_t)hs->d * pl.C * m;
+    float *colmax = reinterpret_cast<float *>(base + pl.off_colmax);
+    if (prec == CMM_PREC_F32) {
+        // the per-column scales of the fixed-point scatter
+        Span sp("colmax", s, 2);
+        e = launch_rowmax((const float *)At, pl.ldat, k, m, colmax, s);
+        if (e == cudaSuccess) e = launch_rowmax((const float *)Bp, pl.ldbp, k, p, colmax + k, s);
+        if (e != cudaSuccess) return cuda_fail(e, "column maxima");
+    }
     if (pl.tmem) {
-        // scatter tables, then the per-column scales of the fixed-point scatter
         {
             Span sp("sketch_tables", s);
             e = launch_sketch_tm_tables(pl, m, p, hs->d, hp, const_cast<tab_t *>(tabA),
                                         const_cast<tab_t *>(tabB), s);
         }
         if (e != cudaSuccess) return cuda_fail(e, "scatter tables");
-        float *colmax = reinterpret_cast<float *>(base + pl.off_colmax);
-        {
-            Span sp("colmax", s, 2);
-            e = launch_rowmax((const float *)At, pl.ldat, k, m, colmax, s);
-            if (e == cudaSuccess) e = launch_rowmax((const float *)Bp, pl.ldbp, k, p, colmax + k, s);
-        }
-        if (e != cudaSuccess) return cuda_fail(e, "column maxima");
         Span sp("sketch_f32", s);
         e = launch_sketch_tm(pl, (const float *)At, (const float *)Bp, m, k, p, hs->d, tabA, tabB,
                              colmax, partial, s);
@@ -302,14 +302,14 @@ int run_sketch(const void *A, int64_t lda, int transA, const void *B, int64_t ld
                 : prec == CMM_PREC_BF16TC ? "sketch_bf16tc" : "sketch_f32", s, 2);
         if (prec == CMM_PREC_F64)
             e = launch_sketch_f64(pl, (const double *)At, (const double *)Bp, m, k, p, hs->d, hp,
-                                  tabA, tabB, partial, s);
+                                  tabA, tabB, nullptr, partial, s);
         else if (prec == CMM_PREC_BF16TC) {
             uint32_t *tA32 = reinterpret_cast<uint32_t *>(base + pl.off_tab);
             e = launch_sketch_bf16(pl, (const float *)At, (const float *)Bp, m, k, p, hs->d, hp,
                                    tA32, tA32 + (size_t)hs->d * pl.C * m, partial, s);
         } else
             e = launch_sketch_f32(pl, (const float *)At, (const float *)Bp, m, k, p, hs->d, hp,
-                                  tabA, tabB, partial, s);
+                                  tabA, tabB, colmax, partial, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "sketch kernel");
     {

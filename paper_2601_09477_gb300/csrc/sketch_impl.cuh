@@ -20,6 +20,16 @@
 // At the end the groups' Z are summed in FP64 and the CTA writes its FP64
 // partial Z for (block, r, slice) -- the cross-block reduction is FP64.
 //
+// FP32 butterflies take the scatter in fixed point: shared-memory FP32 atomic
+// adds are far slower than integer ones, so each column is scattered as the
+// 32-bit integers round(a * 2^e), with one power of two per (CTA, column)
+// such that c_max * max_i |a_i| * 2^e < 2^30 (c_max: the most elements that
+// share a bucket of the CTA's slice, counted once per CTA).  The bucket sums
+// are exact, independent of the order of the atomics and below 2^31; round 0
+// of the transform converts them to FP32 and scales back by 2^-e.  The column
+// maxima come from a separate pass (launch_rowmax).  FP64 butterflies keep
+// FP64 atomics.
+//
 // The scatter either evaluates the hashes per element (multiply-add-shift,
 // two 64-bit products) or, in the single-problem kernel, reads one packed
 // 32-bit word per element from a table built once per call for the CTA's
@@ -94,9 +104,114 @@ __device__ __forceinline__ void scatter_table(T *Sg, const T *__restrict__ col,
     }
 }
 
+// ---- fixed-point scatter (FP32 butterflies) ----
+
+// the power of two 2^e of one column: cmax * colmax * 2^e < 2^30, with e kept
+// in [-126, 126] so that 2^e and 2^-e are normal floats
+__device__ __forceinline__ void fixed_scale(float colmax, int cmax, float &s, float &inv) {
+    // colmax < 2^Ec (exponent field - 126; 0 and subnormals give -126) and
+    // cmax < 2^Ek, so the product is below 2^(Ec + Ek)
+    const int Ec = ((__float_as_int(colmax) >> 23) & 0xff) - 126;
+    const int Ek = 32 - __clz(cmax);
+    const int e = min(max(30 - Ec - Ek, -126), 126);
+    s = __int_as_float((127 + e) << 23);
+    inv = __int_as_float((127 - e) << 23);
+}
+
+// largest number of the n keys that share a bucket of the slice: counted in
+// S0 (an integer view of one zeroed slice, zero again on return) by all
+// THREADS threads; keys from the table when given, else hashed
+template <int L, int LE, int THREADS>
+__device__ __forceinline__ int block_cmax(int *S0, const tab_t *__restrict__ tab, int64_t n,
+                                          uint64_t a, uint64_t c, int shift, int *red) {
+    using S = FwhtShape<float, L, LE>;
+    static_assert(THREADS % 32 == 0 && THREADS <= 1024, "whole warps");
+    for (int64_t i = threadIdx.x; i < n; i += THREADS) {
+        const int w = tab ? (int)(__ldg(tab + i) & 0x7fffu)
+                          : pad_index<float, L, LE>((int)(mas_hash(a, c, (uint64_t)i, shift) &
+                                                          (uint32_t)(S::N - 1)));
+        atomicAdd(S0 + w, 1);
+    }
+    __syncthreads();
+    int mx = 0;
+    for (int i = threadIdx.x; i < S::STRIDE; i += THREADS) {
+        mx = max(mx, S0[i]);
+        S0[i] = 0;
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = 0;
+#pragma unroll
+    for (int w = 0; w < THREADS / 32; ++w) mx = max(mx, red[w]);
+    __syncthreads();
+    return mx;
+}
+
+// fixed-point scatter of one column (hashing), values round(v * s)
+template <int L, int LE>
+__device__ __forceinline__ void scatter_column_fixed(int *Sg, const float *__restrict__ col,
+                                                     int64_t n, uint64_t a, uint64_t c,
+                                                     uint64_t as, uint64_t cs, int shift,
+                                                     uint32_t u_hi, int q, float s) {
+    using S = FwhtShape<float, L, LE>;
+    constexpr int P = S::P;
+    constexpr int B = 8;
+    int64_t i = q;
+    for (; i + (B - 1) * (int64_t)P < n; i += B * (int64_t)P) {
+        float val[B];
+#pragma unroll
+        for (int e = 0; e < B; ++e) val[e] = ld_stream(col + i + e * (int64_t)P);
+#pragma unroll
+        for (int e = 0; e < B; ++e) {
+            const uint64_t x = (uint64_t)(i + e * (int64_t)P);
+            const uint32_t h = mas_hash(a, c, x, shift);
+            const uint32_t neg = mas_sign_bit(as, cs, x) ^ (__popc((h >> L) & u_hi) & 1u);
+            const int iv = __float2int_rn(val[e] * s);
+            atomicAdd(Sg + pad_index<float, L, LE>((int)(h & (S::N - 1))), neg ? -iv : iv);
+        }
+    }
+    for (; i < n; i += P) {
+        const int iv = __float2int_rn(ld_stream(col + i) * s);
+        const uint64_t x = (uint64_t)i;
+        const uint32_t h = mas_hash(a, c, x, shift);
+        const uint32_t neg = mas_sign_bit(as, cs, x) ^ (__popc((h >> L) & u_hi) & 1u);
+        atomicAdd(Sg + pad_index<float, L, LE>((int)(h & (S::N - 1))), neg ? -iv : iv);
+    }
+}
+
+// fixed-point scatter of one column with the packed table, values round(v * s)
+template <int L, int LE, int B = 8>
+__device__ __forceinline__ void scatter_table_fixed(int *Sg, const float *__restrict__ col,
+                                                    const tab_t *__restrict__ tab, int64_t n,
+                                                    int q, float s) {
+    constexpr int P = FwhtShape<float, L, LE>::P;
+    int64_t i = q;
+    for (; i + (B - 1) * (int64_t)P < n; i += B * (int64_t)P) {
+        float val[B];
+        tab_t w[B];
+#pragma unroll
+        for (int e = 0; e < B; ++e) {
+            val[e] = ld_stream(col + i + e * (int64_t)P);
+            w[e] = __ldg(tab + i + e * (int64_t)P);
+        }
+#pragma unroll
+        for (int e = 0; e < B; ++e) {
+            const int iv = __float2int_rn(val[e] * s);
+            atomicAdd(Sg + (w[e] & 0x7fffu), (w[e] >> 15) ? -iv : iv);
+        }
+    }
+    for (; i < n; i += P) {
+        const tab_t w = __ldg(tab + i);
+        const int iv = __float2int_rn(ld_stream(col + i) * s);
+        atomicAdd(Sg + (w & 0x7fffu), (w >> 15) ? -iv : iv);
+    }
+}
+
 // One CTA's work item: repetition r (hash functions H, or the tables tabA /
 // tabB of this (r, u_hi) when not null), frequency slice u_hi, inner indices
-// [t0, t1); writes its FP64 partial Z slice to `out` (N values).
+// [t0, t1); writes its FP64 partial Z slice to `out` (N values).  cmA[t] and
+// cmB[t] are the column maxima of A^T[t] and B[t] (FP32 butterflies only).
 // smem_raw must hold sketch_smem_bytes<L, LE, THREADS, T>() bytes.
 template <typename T, typename TZ, int L, int LE, int THREADS>
 __device__ __forceinline__ void sketch_block(const T *__restrict__ At, int64_t ldat,
@@ -105,19 +220,30 @@ __device__ __forceinline__ void sketch_block(const T *__restrict__ At, int64_t l
                                              int64_t t1, const HashRep &H,
                                              const tab_t *__restrict__ tabA,
                                              const tab_t *__restrict__ tabB,
+                                             const float *__restrict__ cmA,
+                                             const float *__restrict__ cmB,
                                              double *__restrict__ out, unsigned char *smem_raw) {
     using S = FwhtShape<T, L, LE>;
     constexpr int E = S::E, P = S::P, G = THREADS / P;
+    constexpr bool FX = sizeof(T) == 4;   // fixed-point scatter
     static_assert(THREADS % P == 0, "CTA must hold whole groups");
     T *sm = reinterpret_cast<T *>(smem_raw);
+    __shared__ int s_red[32];
 
     const int tid = threadIdx.x;
     const int g = tid / P, q = tid % P;
     T *Sg = sm + g * S::STRIDE;
+    int *Sgi = reinterpret_cast<int *>(Sg);
     const int shift = 64 - Lfull;
 
     for (int i = tid; i < G * S::STRIDE; i += THREADS) sm[i] = T(0);
     __syncthreads();
+    int cmaxA = 0, cmaxB = 0;
+    if constexpr (FX) {
+        int *S0 = reinterpret_cast<int *>(sm);
+        cmaxA = block_cmax<L, LE, THREADS>(S0, tabA, m, H.a1, H.c1, shift, s_red);
+        cmaxB = block_cmax<L, LE, THREADS>(S0, tabB, p, H.a2, H.c2, shift, s_red);
+    }
 
     TZ z[E];
 #pragma unroll
@@ -129,27 +255,48 @@ __device__ __forceinline__ void sketch_block(const T *__restrict__ At, int64_t l
     for (int64_t it = 0; it < iters; ++it) {
         const int64_t t = t0 + it * G + g;
         const bool active = t < t1;
+        float sA = 1.f, invA = 1.f, sB = 1.f, invB = 1.f;
+        if constexpr (FX) {
+            if (active) {
+                fixed_scale(__ldg(cmA + t), cmaxA, sA, invA);
+                fixed_scale(__ldg(cmB + t), cmaxB, sB, invB);
+            }
+        }
         if (active) {
-            if (tabA)
+            if constexpr (FX) {
+                if (tabA)
+                    scatter_table_fixed<L, LE>(Sgi, At + t * ldat, tabA, m, q, sA);
+                else
+                    scatter_column_fixed<L, LE>(Sgi, At + t * ldat, m, H.a1, H.c1, H.as1, H.cs1,
+                                                shift, u_hi, q, sA);
+            } else if (tabA) {
                 scatter_table<T, L, LE>(Sg, At + t * ldat, tabA, m, q);
-            else
+            } else {
                 scatter_column<T, L, LE>(Sg, At + t * ldat, m, H.a1, H.c1, H.as1, H.cs1, shift,
                                          u_hi, q);
+            }
         }
         group_sync<P>(g);
-        fwht_rounds<T, L, LE, 0>(Sg, v, q, g);
+        fwht_rounds<T, L, LE, 0, FX>(Sg, v, q, g, invA);
 #pragma unroll
         for (int j = 0; j < E; ++j) xh[j] = v[j];
         group_sync<P>(g);
         if (active) {
-            if (tabB)
+            if constexpr (FX) {
+                if (tabB)
+                    scatter_table_fixed<L, LE>(Sgi, Bp + t * ldbp, tabB, p, q, sB);
+                else
+                    scatter_column_fixed<L, LE>(Sgi, Bp + t * ldbp, p, H.a2, H.c2, H.as2, H.cs2,
+                                                shift, u_hi, q, sB);
+            } else if (tabB) {
                 scatter_table<T, L, LE>(Sg, Bp + t * ldbp, tabB, p, q);
-            else
+            } else {
                 scatter_column<T, L, LE>(Sg, Bp + t * ldbp, p, H.a2, H.c2, H.as2, H.cs2, shift,
                                          u_hi, q);
+            }
         }
         group_sync<P>(g);
-        fwht_rounds<T, L, LE, 0>(Sg, v, q, g);
+        fwht_rounds<T, L, LE, 0, FX>(Sg, v, q, g, invB);
         if constexpr (sizeof(TZ) == 4 && sizeof(T) == 4 && (E % 2) == 0) {
 #pragma unroll
             for (int j = 0; j < E; j += 2) {
@@ -191,7 +338,8 @@ __global__ void __launch_bounds__(THREADS, (THREADS >= 512 ? 1 : 2))
 sketch_kernel(const T *__restrict__ At, int64_t ldat, const T *__restrict__ Bp, int64_t ldbp,
               int64_t m, int64_t k, int64_t p, int Lfull, int C, int64_t chunk, int d,
               const __grid_constant__ HashParams hp, const tab_t *__restrict__ tabA,
-              const tab_t *__restrict__ tabB, double *__restrict__ partial) {
+              const tab_t *__restrict__ tabB, const float *__restrict__ colmax,
+              double *__restrict__ partial) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int item = blockIdx.x;
     const uint32_t u_hi = (uint32_t)(item % C);
@@ -205,7 +353,8 @@ sketch_kernel(const T *__restrict__ At, int64_t ldat, const T *__restrict__ Bp, 
     const int64_t slot = (int64_t)r * C + u_hi;
     sketch_block<T, TZ, L, LE, THREADS>(At, ldat, Bp, ldbp, m, p, Lfull, u_hi, t0, t1, hp.rep[r],
                                         tabA ? tabA + slot * m : nullptr,
-                                        tabB ? tabB + slot * p : nullptr, out, smem_raw);
+                                        tabB ? tabB + slot * p : nullptr, colmax,
+                                        colmax ? colmax + k : nullptr, out, smem_raw);
 }
 
 // packed scatter words for every (r, u_hi) slot: tab[(r*C + u_hi)*n + x] =
@@ -242,8 +391,8 @@ __global__ void sketch_table_kernel(const __grid_constant__ HashParams hp, int d
 template <typename T, typename TZ, int L, int LE, int THREADS>
 cudaError_t launch_sketch_inst(const SketchPlan &pl, const T *At, const T *Bp, int64_t m,
                                int64_t k, int64_t p, int d, const HashParams &hp,
-                               const tab_t *tabA, const tab_t *tabB, double *partial,
-                               cudaStream_t s) {
+                               const tab_t *tabA, const tab_t *tabB, const float *colmax,
+                               double *partial, cudaStream_t s) {
     if (tabA) {
         const int64_t n = (int64_t)d * pl.C * (m + p);
         int64_t g = (n + 255) / 256;
@@ -261,7 +410,8 @@ cudaError_t launch_sketch_inst(const SketchPlan &pl, const T *At, const T *Bp, i
     if (e != cudaSuccess) return e;
     const int64_t blocks = (int64_t)pl.nchunks * d * pl.C;
     kern<<<(unsigned)blocks, THREADS, pl.smem, s>>>(At, pl.ldat, Bp, pl.ldbp, m, k, p, pl.L,
-                                                    pl.C, pl.chunk, d, hp, tabA, tabB, partial);
+                                                    pl.C, pl.chunk, d, hp, tabA, tabB, colmax,
+                                                    partial);
     return cudaGetLastError();
 }
 

@@ -176,18 +176,6 @@ __device__ __forceinline__ int table_cmax(int *Si, const tab_t *__restrict__ tab
     return mx;
 }
 
-// the power of two 2^e of one column: cmax * colmax * 2^e < 2^30, with e kept
-// in [-126, 126] so that 2^e and 2^-e are normal floats
-__device__ __forceinline__ void fixed_scale(float colmax, int cmax, float &s, float &inv) {
-    // colmax < 2^Ec (exponent field - 126; 0 and subnormals give -126) and
-    // cmax < 2^Ek, so the product is below 2^(Ec + Ek)
-    const int Ec = ((__float_as_int(colmax) >> 23) & 0xff) - 126;
-    const int Ek = 32 - __clz(cmax);
-    const int e = min(max(30 - Ec - Ek, -126), 126);
-    s = __int_as_float((127 + e) << 23);
-    inv = __int_as_float((127 - e) << 23);
-}
-
 // scatter one column as integers round(a * s) with the packed table
 template <int B>
 __device__ __forceinline__ void scatter_fixed(int *Si, const float *__restrict__ col,

@@ -63,6 +63,53 @@ def test_sketch_matches_oracle(cmm, prec, shape):
     assert err <= TOL[prec], err
 
 
+def _extreme_columns(m, k, p, seed):
+    """Columns that stress the FP32 fixed-point scatter (one power-of-two scale
+    per column from its max |value| and the bucket occupancy): a zero column,
+    one dominant entry over tiny ones, constant columns, and column scales from
+    1e-20 to 1e15 with B's row scaled by the inverse so products stay O(1)."""
+    g = np.random.default_rng(seed)
+    A = g.standard_normal((m, k))
+    B = g.standard_normal((k, p))
+    A[:, 0] = 0.0
+    A[:, 1] = 1e-3 * g.standard_normal(m)
+    A[m // 3, 1] = 1e3
+    B[2, :] = 1e-3 * g.standard_normal(p)
+    B[2, 5] = -7e2
+    A[:, 3] = 1.0
+    B[3, :] = -0.5
+    scales = 10.0 ** g.uniform(-20, 15, size=k)
+    scales[:5] = 1.0
+    A *= scales[None, :]
+    B /= scales[:, None]
+    return A, B
+
+
+@pytest.mark.parametrize("L", [12, 14, 15])
+def test_fixed_point_scatter_extreme_columns(cmm, L):
+    m, k, p, d = 1200, 40, 900, 3
+    A, B = _extreme_columns(m, k, p, 7 + L)
+    A32 = A.astype(np.float32).astype(np.float64)
+    B32 = B.astype(np.float32).astype(np.float64)
+    h = cmm.make_hashes(77 + L, d, L)
+    R = cmm.sketch(_dev(A32, torch.float32), _dev(B32, torch.float32), h, prec="f32").cpu().numpy()
+    Ro = orc.compress(A32, B32, h.params, L, nthreads=8)
+    err = np.abs(R - Ro).max() / _norm_scale(A32, B32)
+    assert err <= TOL["f32"], err
+
+
+@pytest.mark.parametrize("L", [12, 16])
+def test_fp32_sketch_is_deterministic(cmm, L):
+    # integer bucket sums and fixed reduction orders: bitwise identical reruns
+    g = np.random.default_rng(L)
+    A = _dev(g.standard_normal((800, 300)), torch.float32)
+    B = _dev(g.standard_normal((300, 700)), torch.float32)
+    h = cmm.make_hashes(5, 3, L)
+    R1 = cmm.sketch(A, B, h, prec="f32")
+    R2 = cmm.sketch(A, B, h, prec="f32")
+    assert torch.equal(R1, R2)
+
+
 @pytest.mark.parametrize("shape", [(1000, 200, 900, 15, 3), (517, 97, 333, 17, 2),
                                    (2048, 300, 1500, 16, 5), (64, 33, 70, 15, 1)])
 def test_sketch_bf16_tensor_core(cmm, shape):
