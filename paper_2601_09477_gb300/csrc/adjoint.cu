@@ -10,6 +10,10 @@
 //     dB[t][j] = s2_r(j) sum_r (G_r XOR-conv x_{r,t})[h2_r(j)],
 // and each XOR convolution is (1/b) H((H G_r) o (H y_{r,t})) (Sec. 3.2).
 //
+// With FP32 butterflies the two scatters are the fixed-point scatter of the
+// sketch kernel (integer bucket sums, per-column power-of-two scales from the
+// column maxima, bucket occupancy counted once per CTA and repetition).
+//
 // Kernels: adj_g_kernel scatters the weights into G (FP64); the FP64 finish
 // pass turns G into Gs = (1/b) H G; adjoint_kernel then, per (t, r) and per
 // frequency slice, rebuilds H x and H y exactly as the sketch kernel does,
@@ -62,9 +66,13 @@ __global__ void __launch_bounds__(THREADS, 1)
 adjoint_kernel(const T *__restrict__ At, int64_t ldat, const T *__restrict__ Bp, int64_t ldbp,
                int64_t m, int64_t k, int64_t p, int Lfull, int C, int64_t chunk, int d,
                const __grid_constant__ HashParams hp, const double *__restrict__ Gs,
-               T *__restrict__ dAt, T *__restrict__ dBt, int accumulate) {
+               const float *__restrict__ colmax, T *__restrict__ dAt, T *__restrict__ dBt,
+               int accumulate) {
     using S = FwhtShape<T, L, LE>;
     constexpr int E = S::E, P = S::P, G = THREADS / P;
+    constexpr bool FX = sizeof(T) == 4;   // fixed-point scatter
+    __shared__ int s_red[32];
+    __shared__ int s_cmax[2 * CMM_MAX_D];
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
     const int tid = threadIdx.x;
@@ -82,6 +90,20 @@ adjoint_kernel(const T *__restrict__ At, int64_t ldat, const T *__restrict__ Bp,
 
     for (int i = tid; i < G * S::STRIDE; i += THREADS) sm[i] = T(0);
     __syncthreads();
+    if constexpr (FX) {
+        int *S0 = reinterpret_cast<int *>(sm);
+        for (int r = 0; r < d; ++r) {
+            const HashRep &H = hp.rep[r];
+            const int ca = block_cmax<L, LE, THREADS>(S0, nullptr, m, H.a1, H.c1, shift, s_red);
+            const int cb = block_cmax<L, LE, THREADS>(S0, nullptr, p, H.a2, H.c2, shift, s_red);
+            if (tid == 0) {
+                s_cmax[r] = ca;
+                s_cmax[CMM_MAX_D + r] = cb;
+            }
+        }
+        __syncthreads();
+    }
+    int *Sgi = reinterpret_cast<int *>(Sg);
 
     T xh[E], v[E], gh[E];
     const int64_t nt = t1 > t0 ? t1 - t0 : 0;
@@ -94,17 +116,33 @@ adjoint_kernel(const T *__restrict__ At, int64_t ldat, const T *__restrict__ Bp,
         for (int r = 0; r < d; ++r) {
             const HashRep H = hp.rep[r];
             // H x_t and H y_t of this slice, as in the sketch kernel
-            if (active) scatter_column<T, L, LE>(Sg, At + t * ldat, m, H.a1, H.c1, H.as1, H.cs1,
-                                                 shift, u_hi, q);
+            float sA = 1.f, invA = 1.f, sB = 1.f, invB = 1.f;
+            if constexpr (FX) {
+                if (active) {
+                    fixed_scale(__ldg(colmax + t), s_cmax[r], sA, invA);
+                    fixed_scale(__ldg(colmax + k + t), s_cmax[CMM_MAX_D + r], sB, invB);
+                    scatter_column_fixed<L, LE>(Sgi, (const float *)(At + t * ldat), m, H.a1,
+                                                H.c1, H.as1, H.cs1, shift, u_hi, q, sA);
+                }
+            } else if (active) {
+                scatter_column<T, L, LE>(Sg, At + t * ldat, m, H.a1, H.c1, H.as1, H.cs1, shift,
+                                         u_hi, q);
+            }
             group_sync<P>(g);
-            fwht_rounds<T, L, LE, 0>(Sg, v, q, g);
+            fwht_rounds<T, L, LE, 0, FX>(Sg, v, q, g, invA);
 #pragma unroll
             for (int j = 0; j < E; ++j) xh[j] = v[j];
             group_sync<P>(g);
-            if (active) scatter_column<T, L, LE>(Sg, Bp + t * ldbp, p, H.a2, H.c2, H.as2, H.cs2,
-                                                 shift, u_hi, q);
+            if constexpr (FX) {
+                if (active)
+                    scatter_column_fixed<L, LE>(Sgi, (const float *)(Bp + t * ldbp), p, H.a2,
+                                                H.c2, H.as2, H.cs2, shift, u_hi, q, sB);
+            } else if (active) {
+                scatter_column<T, L, LE>(Sg, Bp + t * ldbp, p, H.a2, H.c2, H.as2, H.cs2, shift,
+                                         u_hi, q);
+            }
             group_sync<P>(g);
-            fwht_rounds<T, L, LE, 0>(Sg, v, q, g);
+            fwht_rounds<T, L, LE, 0, FX>(Sg, v, q, g, invB);
             const double *gr = Gs + r * b + (int64_t)u_hi * S::N;
 #pragma unroll
             for (int j = 0; j < E; ++j) gh[j] = (T)__ldg(gr + final_index<T, L, LE>(q, j));
@@ -148,14 +186,14 @@ adjoint_kernel(const T *__restrict__ At, int64_t ldat, const T *__restrict__ Bp,
 
 template <typename T, int L, int LE, int THREADS>
 cudaError_t launch_adj_inst(const AdjointPlan &pl, const T *At, const T *Bp, int64_t m, int64_t k,
-                            int64_t p, int d, const HashParams &hp, const double *Gs, T *dAt,
-                            T *dBt, cudaStream_t s) {
+                            int64_t p, int d, const HashParams &hp, const double *Gs,
+                            const float *colmax, T *dAt, T *dBt, cudaStream_t s) {
     auto kern = adjoint_kernel<T, L, LE, THREADS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)pl.smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)((int64_t)pl.nchunks * pl.C), THREADS, pl.smem, s>>>(
-        At, pl.ldat, Bp, pl.ldbp, m, k, p, pl.L, pl.C, pl.chunk, d, hp, Gs, dAt, dBt,
+        At, pl.ldat, Bp, pl.ldbp, m, k, p, pl.L, pl.C, pl.chunk, d, hp, Gs, colmax, dAt, dBt,
         pl.C > 1 ? 1 : 0);
     return cudaGetLastError();
 }
@@ -173,9 +211,11 @@ constexpr int adj_threads() {
 
 template <typename T, int L>
 cudaError_t run_adj(const AdjointPlan &pl, const T *At, const T *Bp, int64_t m, int64_t k, int64_t p,
-                    int d, const HashParams &hp, const double *Gs, T *dAt, T *dBt, cudaStream_t s) {
+                    int d, const HashParams &hp, const double *Gs, const float *colmax, T *dAt,
+                    T *dBt, cudaStream_t s) {
     constexpr int LE = L < AdjCfg<T>::LEmax ? L : AdjCfg<T>::LEmax;
-    return launch_adj_inst<T, L, LE, adj_threads<T, L>()>(pl, At, Bp, m, k, p, d, hp, Gs, dAt, dBt, s);
+    return launch_adj_inst<T, L, LE, adj_threads<T, L>()>(pl, At, Bp, m, k, p, d, hp, Gs, colmax,
+                                                          dAt, dBt, s);
 }
 
 }  // namespace
@@ -211,7 +251,7 @@ cudaError_t launch_adj_g(const HashParams &hp, int d, int L, int64_t P, const in
 
 cudaError_t launch_adjoint(const AdjointPlan &pl, const void *At, const void *Bp, int64_t m,
                            int64_t k, int64_t p, int d, const HashParams &hp, const double *Gs,
-                           void *dAt, void *dBt, cudaStream_t s) {
+                           const float *colmax, void *dAt, void *dBt, cudaStream_t s) {
     if (pl.C > 1) {
         const size_t es = pl.prec == CMM_PREC_F64 ? 8 : 4;
         cudaError_t e = cudaMemsetAsync(dAt, 0, (size_t)k * m * es, s);
@@ -222,7 +262,7 @@ cudaError_t launch_adjoint(const AdjointPlan &pl, const void *At, const void *Bp
         const double *a = (const double *)At, *bb = (const double *)Bp;
         double *da = (double *)dAt, *db = (double *)dBt;
         switch (pl.Llo) {
-#define CASE(L) case L: return run_adj<double, L>(pl, a, bb, m, k, p, d, hp, Gs, da, db, s);
+#define CASE(L) case L: return run_adj<double, L>(pl, a, bb, m, k, p, d, hp, Gs, nullptr, da, db, s);
             CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10)
             CASE(11) CASE(12) CASE(13)
 #undef CASE
@@ -232,7 +272,7 @@ cudaError_t launch_adjoint(const AdjointPlan &pl, const void *At, const void *Bp
     const float *a = (const float *)At, *bb = (const float *)Bp;
     float *da = (float *)dAt, *db = (float *)dBt;
     switch (pl.Llo) {
-#define CASE(L) case L: return run_adj<float, L>(pl, a, bb, m, k, p, d, hp, Gs, da, db, s);
+#define CASE(L) case L: return run_adj<float, L>(pl, a, bb, m, k, p, d, hp, Gs, colmax, da, db, s);
         CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10)
         CASE(11) CASE(12) CASE(13) CASE(14)
 #undef CASE

@@ -56,15 +56,16 @@ struct AdjointPlan {
     size_t smem;
     bool prep_A, prep_B;
     int64_t ldat, ldbp;
-    size_t off_At, off_Bp, off_G, off_Gs, off_Z, off_dAt, off_dBt, total;
+    size_t off_At, off_Bp, off_G, off_Gs, off_Z, off_dAt, off_dBt, off_colmax, total;
 };
 
 int adjoint_threads(int prec, int Llo);
 cudaError_t launch_adj_g(const HashParams &hp, int d, int L, int64_t P, const int32_t *I,
                          const int32_t *J, const double *W, double *G, cudaStream_t s);
+// colmax: the 2k column maxima of the FP32 fixed-point scatter (unused by FP64)
 cudaError_t launch_adjoint(const AdjointPlan &pl, const void *At, const void *Bp, int64_t m,
                            int64_t k, int64_t p, int d, const HashParams &hp, const double *Gs,
-                           void *dAt, void *dBt, cudaStream_t s);
+                           const float *colmax, void *dAt, void *dBt, cudaStream_t s);
 // dst (dst_dtype, leading dimension ldd) = src (rows x cols, FP64 when src_f64
 // else FP32, contiguous), transposed when `transpose`
 cudaError_t launch_convert_out(const void *src, int src_f64, int64_t rows, int64_t cols,

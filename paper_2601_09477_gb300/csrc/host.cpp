@@ -443,6 +443,8 @@ bool plan_adjoint(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int 
     off += align_up((size_t)k * m * es);
     pl.off_dBt = off;
     off += align_up((size_t)k * p * es);
+    pl.off_colmax = off;
+    if (!f64) off += align_up((size_t)2 * k * sizeof(float));
     pl.total = off;
     return true;
 }
@@ -817,9 +819,16 @@ int cmm_backward(const void *A, int64_t lda, int32_t transA, const void *B, int6
     }
     if (e != cudaSuccess) return cuda_fail(e, "adjoint weight transform");
     void *dAt = base + pl.off_dAt, *dBt = base + pl.off_dBt;
+    float *colmax = reinterpret_cast<float *>(base + pl.off_colmax);
+    if (prec == CMM_PREC_F32) {
+        Span sp("colmax", s, 2);
+        e = launch_rowmax((const float *)At, pl.ldat, k, m, colmax, s);
+        if (e == cudaSuccess) e = launch_rowmax((const float *)Bp, pl.ldbp, k, p, colmax + k, s);
+        if (e != cudaSuccess) return cuda_fail(e, "column maxima");
+    }
     {
         Span sp(prec == CMM_PREC_F64 ? "adjoint_f64" : "adjoint_f32", s);
-        e = launch_adjoint(pl, At, Bp, m, k, p, hs->d, hp, Gs, dAt, dBt, s);
+        e = launch_adjoint(pl, At, Bp, m, k, p, hs->d, hp, Gs, colmax, dAt, dBt, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "adjoint kernel");
     {

@@ -176,6 +176,14 @@ __device__ __forceinline__ int table_cmax(int *Si, const tab_t *__restrict__ tab
     return mx;
 }
 
+// one element of the fixed-point scatter: table word w (bucket word in bits
+// 0-14, sign in bit 15); the sign is applied by flipping the sign bit of the
+// scale, so round(v * s) is taken once and the atomic adds an integer
+__device__ __forceinline__ void scatter_one(int *Si, uint32_t w, float v, uint32_t sbits) {
+    const float sc = __uint_as_float(sbits ^ ((w << 16) & 0x80000000u));
+    atomicAdd(Si + (w & 0x7fffu), __float2int_rn(v * sc));
+}
+
 // scatter one column as integers round(a * s) with the packed table
 template <int B>
 __device__ __forceinline__ void scatter_fixed(int *Si, const float *__restrict__ col,
@@ -191,15 +199,45 @@ __device__ __forceinline__ void scatter_fixed(int *Si, const float *__restrict__
             w[e] = __ldg(tab + i + e * (int64_t)kTmP);
         }
 #pragma unroll
-        for (int e = 0; e < B; ++e) {
-            const int iv = __float2int_rn(val[e] * s);
-            atomicAdd(Si + (w[e] & 0x7fffu), (w[e] >> 15) ? -iv : iv);
+        for (int e = 0; e < B; ++e) scatter_one(Si, w[e], val[e], __float_as_uint(s));
+    }
+    for (; i < n; i += kTmP) scatter_one(Si, __ldg(tab + i), ld_stream(col + i), __float_as_uint(s));
+}
+
+// vectorised variant: n % 4 == 0, col 16-byte and tab 8-byte aligned; thread
+// q takes elements 4i .. 4i+3 for i = q, q + 128, ...
+template <int BV>
+__device__ __forceinline__ void scatter_fixed_v4(int *Si, const float *__restrict__ col,
+                                                 const tab_t *__restrict__ tab, int64_t n, int q,
+                                                 float s) {
+    const float4 *c4 = reinterpret_cast<const float4 *>(col);
+    const uint2 *t4 = reinterpret_cast<const uint2 *>(tab);
+    const uint32_t sb = __float_as_uint(s);
+    const int64_t n4 = n >> 2;
+    int64_t i = q;
+    for (; i + (BV - 1) * (int64_t)kTmP < n4; i += BV * (int64_t)kTmP) {
+        float4 val[BV];
+        uint2 w[BV];
+#pragma unroll
+        for (int e = 0; e < BV; ++e) {
+            val[e] = __ldcs(c4 + i + e * (int64_t)kTmP);
+            w[e] = __ldg(t4 + i + e * (int64_t)kTmP);
+        }
+#pragma unroll
+        for (int e = 0; e < BV; ++e) {
+            scatter_one(Si, w[e].x & 0xffffu, val[e].x, sb);
+            scatter_one(Si, w[e].x >> 16, val[e].y, sb);
+            scatter_one(Si, w[e].y & 0xffffu, val[e].z, sb);
+            scatter_one(Si, w[e].y >> 16, val[e].w, sb);
         }
     }
-    for (; i < n; i += kTmP) {
-        const tab_t w = __ldg(tab + i);
-        const int iv = __float2int_rn(ld_stream(col + i) * s);
-        atomicAdd(Si + (w & 0x7fffu), (w >> 15) ? -iv : iv);
+    for (; i < n4; i += kTmP) {
+        const float4 v = __ldcs(c4 + i);
+        const uint2 w = __ldg(t4 + i);
+        scatter_one(Si, w.x & 0xffffu, v.x, sb);
+        scatter_one(Si, w.x >> 16, v.y, sb);
+        scatter_one(Si, w.y & 0xffffu, v.z, sb);
+        scatter_one(Si, w.y >> 16, v.w, sb);
     }
 }
 
@@ -207,7 +245,7 @@ __global__ void __launch_bounds__(kTmP, 2)
 sketch_tm_kernel(const float *__restrict__ At, int64_t ldat, const float *__restrict__ Bp,
                  int64_t ldbp, int64_t m, int64_t k, int64_t p, int Lfull, int C, int64_t chunk,
                  int d, const tab_t *__restrict__ tabA, const tab_t *__restrict__ tabB,
-                 const float *__restrict__ colmax, double *__restrict__ partial) {
+                 const float *__restrict__ colmax, double *__restrict__ partial, int vec4) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *S = reinterpret_cast<float *>(smem_raw);
     int *Si = reinterpret_cast<int *>(smem_raw);
@@ -256,37 +294,46 @@ sketch_tm_kernel(const float *__restrict__ At, int64_t ldat, const float *__rest
 
     float v[kTmE];
     for (int64_t t = t0; t < t1; ++t) {
-        // all of a thread's column values are loaded before its atomics
-        // (the registers of v are free during the scatter)
-        float sA, invA, sB, invB;
-        fixed_scale(__ldg(colmax + t), cmaxA, sA, invA);
-        fixed_scale(__ldg(colmax + k + t), cmaxB, sB, invB);
-        scatter_fixed<32>(Si, At + t * ldat, tA, m, q, sA);
-        __syncthreads();
-        tm_fwht(S, v, q, invA);
+        // half 0: x_t = sketch of A^T[t] -> H x_t into TMEM; half 1: y_t ->
+        // Z += H x_t o H y_t.  The halves share one copy of the scatter and
+        // transform code (a rolled loop keeps the unrolled transform out of
+        // the instruction cache twice).  A thread's column values are all
+        // loaded before its atomics (the registers of v are free then).
+#pragma unroll 1
+        for (int half = 0; half < 2; ++half) {
+            float sc, inv;
+            fixed_scale(__ldg(colmax + (half ? k : 0) + t), half ? cmaxB : cmaxA, sc, inv);
+            const float *col = half ? Bp + t * ldbp : At + t * ldat;
+            const tab_t *tab = half ? tB : tA;
+            const int64_t n = half ? p : m;
+            if (vec4)
+                scatter_fixed_v4<8>(Si, col, tab, n, q, sc);
+            else
+                scatter_fixed<32>(Si, col, tab, n, q, sc);
+            __syncthreads();
+            tm_fwht(S, v, q, inv);
+            if (half == 0) {
 #pragma unroll
-        for (int c = 0; c < kTmE / 16; ++c) tmem_st16_nowait(tx + 16 * c, v + 16 * c);
-        tmem_wait_st();
-        __syncthreads();
-        scatter_fixed<32>(Si, Bp + t * ldbp, tB, p, q, sB);
-        __syncthreads();
-        tm_fwht(S, v, q, invB);
+                for (int c = 0; c < kTmE / 16; ++c) tmem_st16_nowait(tx + 16 * c, v + 16 * c);
+            } else {
 #pragma unroll
-        for (int c = 0; c < kTmE / 16; ++c) {
-            float xs[16], zs[16];
-            tmem_ld16x2(tx + 16 * c, xs, tz + 16 * c, zs);
+                for (int c = 0; c < kTmE / 16; ++c) {
+                    float xs[16], zs[16];
+                    tmem_ld16x2(tx + 16 * c, xs, tz + 16 * c, zs);
 #pragma unroll
-            for (int e = 0; e < 16; e += 2) {
-                const float2 acc = __ffma2_rn(make_float2(xs[e], xs[e + 1]),
-                                              make_float2(v[16 * c + e], v[16 * c + e + 1]),
-                                              make_float2(zs[e], zs[e + 1]));
-                zs[e] = acc.x;
-                zs[e + 1] = acc.y;
+                    for (int e = 0; e < 16; e += 2) {
+                        const float2 acc = __ffma2_rn(make_float2(xs[e], xs[e + 1]),
+                                                      make_float2(v[16 * c + e], v[16 * c + e + 1]),
+                                                      make_float2(zs[e], zs[e + 1]));
+                        zs[e] = acc.x;
+                        zs[e + 1] = acc.y;
+                    }
+                    tmem_st16_nowait(tz + 16 * c, zs);
+                }
             }
-            tmem_st16_nowait(tz + 16 * c, zs);
+            tmem_wait_st();
+            __syncthreads();
         }
-        tmem_wait_st();
-        __syncthreads();
     }
 
 #pragma unroll
@@ -332,9 +379,16 @@ cudaError_t launch_sketch_tm(const SketchPlan &pl, const float *At, const float 
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmSmem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (int64_t)pl.nchunks * d * pl.C;
+    // vector loads need 16-byte aligned rows of whole float4s (the tables are
+    // then 8-byte aligned: slot offsets are multiples of 4 words)
+    const bool vec4 = m % 4 == 0 && p % 4 == 0 && pl.ldat % 4 == 0 && pl.ldbp % 4 == 0 &&
+                      reinterpret_cast<uintptr_t>(At) % 16 == 0 &&
+                      reinterpret_cast<uintptr_t>(Bp) % 16 == 0 &&
+                      reinterpret_cast<uintptr_t>(tabA) % 8 == 0 &&
+                      reinterpret_cast<uintptr_t>(tabB) % 8 == 0;
     sketch_tm_kernel<<<(unsigned)blocks, kTmP, kTmSmem, s>>>(At, pl.ldat, Bp, pl.ldbp, m, k, p,
                                                              pl.L, pl.C, pl.chunk, d, tabA, tabB,
-                                                             colmax, partial);
+                                                             colmax, partial, vec4 ? 1 : 0);
     return cudaGetLastError();
 }
 
