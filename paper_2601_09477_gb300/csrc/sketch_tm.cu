@@ -307,7 +307,7 @@ sketch_tm_kernel(const float *__restrict__ At, int64_t ldat, const float *__rest
             const tab_t *tab = half ? tB : tA;
             const int64_t n = half ? p : m;
             if (vec4)
-                scatter_fixed_v4<8>(Si, col, tab, n, q, sc);
+                scatter_fixed_v4<16>(Si, col, tab, n, q, sc);
             else
                 scatter_fixed<32>(Si, col, tab, n, q, sc);
             __syncthreads();
