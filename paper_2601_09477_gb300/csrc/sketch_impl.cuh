@@ -72,12 +72,20 @@ __device__ __forceinline__ void scatter_column(T *Sg, const T *__restrict__ col,
             atomicAdd(Sg + pad_index<T, L, LE>((int)(h & (S::N - 1))), neg_if(val[e], neg));
         }
     }
-    for (; i < n; i += P) {
-        const T v = ld_stream(col + i);
-        const uint64_t x = (uint64_t)i;
-        const uint32_t h = mas_hash(a, c, x, shift);
-        const uint32_t neg = mas_sign_bit(as, cs, x) ^ (__popc((h >> L) & u_hi) & 1u);
-        atomicAdd(Sg + pad_index<T, L, LE>((int)(h & (S::N - 1))), neg_if(v, neg));
+    if (i < n) {   // the last, partial batch: all loads first
+        T val[B];
+#pragma unroll
+        for (int e = 0; e < B; ++e)
+            val[e] = i + e * (int64_t)P < n ? ld_stream(col + i + e * (int64_t)P) : T(0);
+#pragma unroll
+        for (int e = 0; e < B; ++e) {
+            if (i + e * (int64_t)P < n) {
+                const uint64_t x = (uint64_t)(i + e * (int64_t)P);
+                const uint32_t h = mas_hash(a, c, x, shift);
+                const uint32_t neg = mas_sign_bit(as, cs, x) ^ (__popc((h >> L) & u_hi) & 1u);
+                atomicAdd(Sg + pad_index<T, L, LE>((int)(h & (S::N - 1))), neg_if(val[e], neg));
+            }
+        }
     }
 }
 
@@ -98,9 +106,19 @@ __device__ __forceinline__ void scatter_table(T *Sg, const T *__restrict__ col,
 #pragma unroll
         for (int e = 0; e < B; ++e) atomicAdd(Sg + (w[e] & 0x7fffu), neg_if(val[e], (uint32_t)(w[e] >> 15)));
     }
-    for (; i < n; i += P) {
-        const tab_t w = __ldg(tab + i);
-        atomicAdd(Sg + (w & 0x7fffu), neg_if(ld_stream(col + i), (uint32_t)(w >> 15)));
+    if (i < n) {   // the last, partial batch: all loads first
+        T val[B];
+        tab_t w[B];
+#pragma unroll
+        for (int e = 0; e < B; ++e) {
+            const bool ok = i + e * (int64_t)P < n;
+            val[e] = ok ? ld_stream(col + i + e * (int64_t)P) : T(0);
+            w[e] = ok ? __ldg(tab + i + e * (int64_t)P) : (tab_t)0;
+        }
+#pragma unroll
+        for (int e = 0; e < B; ++e)
+            if (i + e * (int64_t)P < n)
+                atomicAdd(Sg + (w[e] & 0x7fffu), neg_if(val[e], (uint32_t)(w[e] >> 15)));
     }
 }
 
@@ -171,12 +189,21 @@ __device__ __forceinline__ void scatter_column_fixed(int *Sg, const float *__res
             atomicAdd(Sg + pad_index<float, L, LE>((int)(h & (S::N - 1))), neg ? -iv : iv);
         }
     }
-    for (; i < n; i += P) {
-        const int iv = __float2int_rn(ld_stream(col + i) * s);
-        const uint64_t x = (uint64_t)i;
-        const uint32_t h = mas_hash(a, c, x, shift);
-        const uint32_t neg = mas_sign_bit(as, cs, x) ^ (__popc((h >> L) & u_hi) & 1u);
-        atomicAdd(Sg + pad_index<float, L, LE>((int)(h & (S::N - 1))), neg ? -iv : iv);
+    if (i < n) {   // the last, partial batch: all loads first
+        float val[B];
+#pragma unroll
+        for (int e = 0; e < B; ++e)
+            val[e] = i + e * (int64_t)P < n ? ld_stream(col + i + e * (int64_t)P) : 0.f;
+#pragma unroll
+        for (int e = 0; e < B; ++e) {
+            if (i + e * (int64_t)P < n) {
+                const uint64_t x = (uint64_t)(i + e * (int64_t)P);
+                const uint32_t h = mas_hash(a, c, x, shift);
+                const uint32_t neg = mas_sign_bit(as, cs, x) ^ (__popc((h >> L) & u_hi) & 1u);
+                const int iv = __float2int_rn(val[e] * s);
+                atomicAdd(Sg + pad_index<float, L, LE>((int)(h & (S::N - 1))), neg ? -iv : iv);
+            }
+        }
     }
 }
 
@@ -201,10 +228,22 @@ __device__ __forceinline__ void scatter_table_fixed(int *Sg, const float *__rest
             atomicAdd(Sg + (w[e] & 0x7fffu), (w[e] >> 15) ? -iv : iv);
         }
     }
-    for (; i < n; i += P) {
-        const tab_t w = __ldg(tab + i);
-        const int iv = __float2int_rn(ld_stream(col + i) * s);
-        atomicAdd(Sg + (w & 0x7fffu), (w >> 15) ? -iv : iv);
+    if (i < n) {   // the last, partial batch: all loads first
+        float val[B];
+        tab_t w[B];
+#pragma unroll
+        for (int e = 0; e < B; ++e) {
+            const bool ok = i + e * (int64_t)P < n;
+            val[e] = ok ? ld_stream(col + i + e * (int64_t)P) : 0.f;
+            w[e] = ok ? __ldg(tab + i + e * (int64_t)P) : (tab_t)0;
+        }
+#pragma unroll
+        for (int e = 0; e < B; ++e) {
+            if (i + e * (int64_t)P < n) {
+                const int iv = __float2int_rn(val[e] * s);
+                atomicAdd(Sg + (w[e] & 0x7fffu), (w[e] >> 15) ? -iv : iv);
+            }
+        }
     }
 }
 

@@ -42,6 +42,7 @@ SHAPES = [
     (513, 300, 411, 13, 3),
     (700, 260, 650, 14, 3),
     (1000, 200, 900, 15, 3),     # two FP32 slices (four FP64 slices)
+    (300, 40, 9000, 14, 2),      # a B row longer than one scatter batch
     (517, 97, 333, 17, 2),       # 8 / 16 slices, even d
     (64, 1000, 50, 3, 1),        # tiny transform, many inner indices
     (1, 5, 1, 1, 1),             # b = 2
@@ -152,16 +153,18 @@ np.savez(sys.argv[7], A=A, B=B, R=R.cpu().numpy(), hp=h.params)
 """
 
 
-@pytest.mark.parametrize("shape", [(700, 260, 650, 14, 3), (300, 70, 500, 16, 2)])
-def test_register_only_sketch_kernel(cmm, shape, tmp_path):
+@pytest.mark.parametrize("kernel", ["regs"])
+@pytest.mark.parametrize("shape", [(700, 260, 650, 14, 3), (300, 70, 500, 16, 2),
+                                   (1024, 100, 2048, 16, 3)])
+def test_alternative_sketch_kernels(cmm, shape, kernel, tmp_path):
     # the FP32 2^14-slice sketch has a TMEM kernel (default) and a register-only
     # kernel (CMM_SKETCH_KERNEL=regs); the second runs in a fresh process
     import os
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    out = str(tmp_path / "regs.npz")
-    env = dict(os.environ, CMM_SKETCH_KERNEL="regs")
+    out = str(tmp_path / "alt.npz")
+    env = dict(os.environ, CMM_SKETCH_KERNEL=kernel)
     subprocess.run([sys.executable, "-c", _REGS_SCRIPT, root] + [str(x) for x in shape] + [out],
                    check=True, env=env)
     z = np.load(out)
