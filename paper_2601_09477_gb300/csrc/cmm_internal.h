@@ -109,13 +109,14 @@ cudaError_t launch_sketch_tm_tables(const SketchPlan &pl, int64_t m, int64_t p, 
 cudaError_t launch_sketch_tm(const SketchPlan &pl, const float *At, const float *Bp, int64_t m,
                              int64_t k, int64_t p, int d, const tab_t *tabA, const tab_t *tabB,
                              const float *colmax, double *partial, cudaStream_t s);
-// BF16 tensor-core variant (2^15-point slices, 32-bit scatter tables)
+// BF16 tensor-core variant (2^15-point slices, fixed-point scatter; colmax as
+// for the FP32 kernels)
 int sketch_bf16_llo();
 int sketch_bf16_threads();
 size_t sketch_bf16_smem();
 cudaError_t launch_sketch_bf16(const SketchPlan &pl, const float *At, const float *Bp, int64_t m,
-                               int64_t k, int64_t p, int d, const HashParams &hp, uint32_t *tabA,
-                               uint32_t *tabB, double *partial, cudaStream_t s);
+                               int64_t k, int64_t p, int d, const HashParams &hp, tab_t *tabA,
+                               tab_t *tabB, const float *colmax, double *partial, cudaStream_t s);
 int sketch_threads_f32(int Llo);
 int sketch_threads_f64(int Llo);
 size_t sketch_smem_f32(int Llo);

@@ -198,9 +198,9 @@ bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int p
     pl.off_Z = off;
     off += align_up((size_t)d * b * sizeof(double));
     pl.off_tab = off;
-    off += align_up((size_t)d * pl.C * (m + p) * (bf16 ? sizeof(uint32_t) : sizeof(tab_t)));
+    off += align_up((size_t)d * pl.C * (m + p) * sizeof(tab_t));
     pl.off_colmax = off;
-    if (prec == CMM_PREC_F32) off += align_up((size_t)2 * k * sizeof(float));
+    if (prec != CMM_PREC_F64) off += align_up((size_t)2 * k * sizeof(float));
     pl.total = off;
     return true;
 }
@@ -279,7 +279,7 @@ int run_sketch(const void *A, int64_t lda, int transA, const void *B, int64_t ld
     const tab_t *tabA = reinterpret_cast<const tab_t *>(base + pl.off_tab);
     const tab_t *tabB = tabA + (size_t)hs->d * pl.C * m;
     float *colmax = reinterpret_cast<float *>(base + pl.off_colmax);
-    if (prec == CMM_PREC_F32) {
+    if (prec != CMM_PREC_F64) {
         // the per-column scales of the fixed-point scatter
         Span sp("colmax", s, 2);
         e = launch_rowmax((const float *)At, pl.ldat, k, m, colmax, s);
@@ -303,11 +303,11 @@ int run_sketch(const void *A, int64_t lda, int transA, const void *B, int64_t ld
         if (prec == CMM_PREC_F64)
             e = launch_sketch_f64(pl, (const double *)At, (const double *)Bp, m, k, p, hs->d, hp,
                                   tabA, tabB, nullptr, partial, s);
-        else if (prec == CMM_PREC_BF16TC) {
-            uint32_t *tA32 = reinterpret_cast<uint32_t *>(base + pl.off_tab);
+        else if (prec == CMM_PREC_BF16TC)
             e = launch_sketch_bf16(pl, (const float *)At, (const float *)Bp, m, k, p, hs->d, hp,
-                                   tA32, tA32 + (size_t)hs->d * pl.C * m, partial, s);
-        } else
+                                   const_cast<tab_t *>(tabA), const_cast<tab_t *>(tabB), colmax,
+                                   partial, s);
+        else
             e = launch_sketch_f32(pl, (const float *)At, (const float *)Bp, m, k, p, hs->d, hp,
                                   tabA, tabB, colmax, partial, s);
     }

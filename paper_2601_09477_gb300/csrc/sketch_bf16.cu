@@ -13,14 +13,19 @@
 //                      n = e + 2 f becomes H16 X2 (H8 (x) I2): bits 8-11 by
 //                      H16, bits 12-14 by H8 while bit 0 (already transformed
 //                      in pass 1) passes through the identity factor.
-// H16, H8 (x) I2 hold only 0 and +-1, exact in BF16.  Rounding happens where a
-// value becomes a BF16 operand: the scatter (BF16 shared-memory atomics), the
-// product inputs of both passes, and the slice between the passes.  H x_t and
-// the running sum Z stay FP32 in tensor memory (TMEM), one lane per thread.
+// H16, H8 (x) I2 hold only 0 and +-1, exact in BF16.  The scatter is the
+// fixed-point integer scatter of the FP32 kernels (per-column power-of-two
+// scale, exact bucket sums); rounding happens where a value becomes a BF16
+// operand: once per bucket when pass 1 reads the integer slice, the product
+// inputs of pass 2, and the slice between the passes.  H x_t and the running
+// sum Z stay FP32 in tensor memory (TMEM), one lane per thread.
 //
-// Shared-memory layout (BF16 elements): u at u + 2 * ((u >> 8) + 7 * (u >> 12));
-// pass-2 loads and zeroing are bank-conflict free, pass-1 loads and stores are
-// 2-way conflicted.
+// Shared memory: the integer slice (2^15 words, element u at word
+// u ^ (((u >> 4) & 3) << 3): pass 1's 64-bit loads of a half-warp hit 32
+// distinct banks; pass 1 clears what it reads), then the BF16 slice between
+// the passes (u at u + 2 * ((u >> 8) + 7 * (u >> 12)); pass-2 loads are
+// bank-conflict free, pass-1 stores 2-way conflicted; fully rewritten by every
+// pass 1, so never cleared).
 #include <cuda_bf16.h>
 
 #include "cmm_internal.h"
@@ -37,8 +42,13 @@ constexpr int kBWarps = kBThreads / 32;
 constexpr int kBTiles = kBN / 256;             // 128 tiles of 256 per pass
 constexpr int kBTilesPerWarp = kBTiles / kBWarps;   // 8
 constexpr int kBElems = kBN + 2 * (127 + 7 * 7) + 2;   // padded BF16 elements
-constexpr size_t kBSmem = ((size_t)kBElems * 2 + 15) / 16 * 16 + 16;
+constexpr size_t kBIntBytes = (size_t)kBN * 4;          // the integer scatter slice
+constexpr size_t kBBfBytes = ((size_t)kBElems * 2 + 15) / 16 * 16;
+constexpr size_t kBSmem = kBIntBytes + kBBfBytes + 128;  // + TMEM address, 16 reduction words
 constexpr uint32_t kBCols = 512;               // whole TMEM: 4 warps per lane quadrant x 128
+
+// word of element u in the integer slice (a bijection on [0, 2^15))
+__host__ __device__ constexpr int bf_swz(int u) { return u ^ (((u >> 4) & 3) << 3); }
 
 // padded element index: non-decreasing pad (so the map is injective); the
 // pass-2 accesses of a warp fall into 16 distinct banks
@@ -135,12 +145,17 @@ __device__ __forceinline__ void tile_pass(const HFrags &f, const uint32_t (&xb)[
     mma_bf16(d2[1], a, bop[1]);
 }
 
+// two integer bucket sums -> FP32 (scaled by inv) -> packed BF16 pair
+__device__ __forceinline__ uint32_t int2_to_bf16x2(int2 w, float inv) {
+    return pack_bf16(__int2float_rn(w.x) * inv, __int2float_rn(w.y) * inv);
+}
+
 // the 2^15-point transform of the slice; `sink(i, vals)` receives, for the
-// warp's i-th pass-2 tile, the 8 FP32 outputs of this thread.  The slice is
-// left zeroed.
+// warp's i-th pass-2 tile, the 8 FP32 outputs of this thread.  Pass 1 reads
+// (and clears) the integer slice Si, scaled by inv.
 template <typename Sink>
-__device__ __forceinline__ void bf_fwht(__nv_bfloat16 *S, const HFrags &f, int warp, int g, int c,
-                                        Sink sink) {
+__device__ __forceinline__ void bf_fwht(int *Si, __nv_bfloat16 *S, const HFrags &f, int warp,
+                                        int g, int c, float inv, Sink sink) {
     uint16_t *S16 = reinterpret_cast<uint16_t *>(S);
     // pass 1: tiles tau = warp * 8 + i, u = a + 16 b + 256 tau
 #pragma unroll 2
@@ -151,8 +166,13 @@ __device__ __forceinline__ void bf_fwht(__nv_bfloat16 *S, const HFrags &f, int w
         for (int h = 0; h < 2; ++h) {
             const int b = 8 * h + g;
             const int u0 = 2 * c + 16 * b + 256 * tau;
-            xb[h][0] = *reinterpret_cast<const uint32_t *>(S + bf_pad(u0));
-            xb[h][1] = *reinterpret_cast<const uint32_t *>(S + bf_pad(u0 + 8));
+            int2 *p0 = reinterpret_cast<int2 *>(Si + bf_swz(u0));       // elements u0, u0 + 1
+            int2 *p1 = reinterpret_cast<int2 *>(Si + bf_swz(u0 + 8));   // u0 + 8, u0 + 9
+            const int2 w0 = *p0, w1 = *p1;
+            *p0 = make_int2(0, 0);
+            *p1 = make_int2(0, 0);
+            xb[h][0] = int2_to_bf16x2(w0, inv);
+            xb[h][1] = int2_to_bf16x2(w1, inv);
         }
         float d2[2][4];
         tile_pass(f, xb, f.hB, d2);
@@ -186,10 +206,6 @@ __device__ __forceinline__ void bf_fwht(__nv_bfloat16 *S, const HFrags &f, int w
             const uint32_t vc = S16[bf_pad(uc)], vd = S16[bf_pad(ud)];
             xb[h][0] = va | (vb << 16);
             xb[h][1] = vc | (vd << 16);
-            S16[bf_pad(ua)] = 0;
-            S16[bf_pad(ub)] = 0;
-            S16[bf_pad(uc)] = 0;
-            S16[bf_pad(ud)] = 0;
         }
         float d2[2][4];
         tile_pass(f, xb, f.mB, d2);
@@ -211,37 +227,100 @@ __device__ __forceinline__ int bf_out_index(int warp, int g, int c, int i, int v
     return (n & 1) + 2 * taup + 256 * a2 + 4096 * (n >> 1);
 }
 
-__device__ __forceinline__ void scatter_bf16(__nv_bfloat16 *S, const float *__restrict__ col,
-                                             const uint32_t *__restrict__ tab, int64_t n, int q) {
+// one element of the fixed-point scatter: table word w (slice word in bits
+// 0-14, sign in bit 15), sign applied by flipping the scale's sign bit
+__device__ __forceinline__ void bf_scatter_one(int *Si, uint32_t w, float v, uint32_t sbits) {
+    const float sc = __uint_as_float(sbits ^ ((w << 16) & 0x80000000u));
+    atomicAdd(Si + (w & 0x7fffu), __float2int_rn(v * sc));
+}
+
+// scatter one column as integers round(v * s); all loads of a batch first
+__device__ __forceinline__ void scatter_bf16(int *Si, const float *__restrict__ col,
+                                             const tab_t *__restrict__ tab, int64_t n, int q,
+                                             float s, int vec4) {
+    const uint32_t sb = __float_as_uint(s);
+    if (vec4) {   // n % 4 == 0, col 16-byte and tab 8-byte aligned
+        constexpr int BV = 4;
+        const float4 *c4 = reinterpret_cast<const float4 *>(col);
+        const uint2 *t4 = reinterpret_cast<const uint2 *>(tab);
+        const int64_t n4 = n >> 2;
+        for (int64_t i = q; i < n4; i += BV * (int64_t)kBThreads) {
+            float4 val[BV];
+            uint2 w[BV];
+#pragma unroll
+            for (int e = 0; e < BV; ++e) {
+                const bool ok = i + e * (int64_t)kBThreads < n4;
+                val[e] = ok ? __ldcs(c4 + i + e * (int64_t)kBThreads) : make_float4(0.f, 0.f, 0.f, 0.f);
+                w[e] = ok ? __ldg(t4 + i + e * (int64_t)kBThreads) : make_uint2(0u, 0u);
+            }
+#pragma unroll
+            for (int e = 0; e < BV; ++e) {
+                if (i + e * (int64_t)kBThreads < n4) {
+                    bf_scatter_one(Si, w[e].x & 0xffffu, val[e].x, sb);
+                    bf_scatter_one(Si, w[e].x >> 16, val[e].y, sb);
+                    bf_scatter_one(Si, w[e].y & 0xffffu, val[e].z, sb);
+                    bf_scatter_one(Si, w[e].y >> 16, val[e].w, sb);
+                }
+            }
+        }
+        return;
+    }
     constexpr int B = 8;
-    int64_t i = q;
-    for (; i + (B - 1) * (int64_t)kBThreads < n; i += B * (int64_t)kBThreads) {
+    for (int64_t i = q; i < n; i += B * (int64_t)kBThreads) {
         float val[B];
-        uint32_t w[B];
+        tab_t w[B];
 #pragma unroll
         for (int e = 0; e < B; ++e) {
-            val[e] = __ldcs(col + i + e * (int64_t)kBThreads);
-            w[e] = __ldg(tab + i + e * (int64_t)kBThreads);
+            const bool ok = i + e * (int64_t)kBThreads < n;
+            val[e] = ok ? __ldcs(col + i + e * (int64_t)kBThreads) : 0.f;
+            w[e] = ok ? __ldg(tab + i + e * (int64_t)kBThreads) : (tab_t)0;
         }
 #pragma unroll
         for (int e = 0; e < B; ++e)
-            atomicAdd(S + (w[e] & 0x7fffffffu), __float2bfloat16_rn((w[e] >> 31) ? -val[e] : val[e]));
+            if (i + e * (int64_t)kBThreads < n) bf_scatter_one(Si, w[e], val[e], sb);
     }
-    for (; i < n; i += kBThreads) {
-        const uint32_t w = __ldg(tab + i);
-        const float v = __ldcs(col + i);
-        atomicAdd(S + (w & 0x7fffffffu), __float2bfloat16_rn((w >> 31) ? -v : v));
+}
+
+// largest number of table entries sharing a bucket (Si zero on entry and on
+// return); all threads of the CTA
+__device__ __forceinline__ int bf_cmax(int *Si, const tab_t *__restrict__ tab, int64_t n, int q,
+                                       int *red) {
+    for (int64_t i = q; i < n; i += kBThreads) atomicAdd(Si + (__ldg(tab + i) & 0x7fffu), 1);
+    __syncthreads();
+    int mx = 0;
+    for (int i = q; i < kBN; i += kBThreads) {
+        mx = max(mx, Si[i]);
+        Si[i] = 0;
     }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((q & 31) == 0) red[q >> 5] = mx;
+    __syncthreads();
+    mx = 0;
+#pragma unroll
+    for (int w = 0; w < kBWarps; ++w) mx = max(mx, red[w]);
+    __syncthreads();
+    return mx;
+}
+
+// 2^e with cmax * colmax * 2^e < 2^30, e in [-126, 126]
+__device__ __forceinline__ void bf_scale(float colmax, int cmax, float &s, float &inv) {
+    const int Ec = ((__float_as_int(colmax) >> 23) & 0xff) - 126;
+    const int Ek = 32 - __clz(cmax);
+    const int e = min(max(30 - Ec - Ek, -126), 126);
+    s = __int_as_float((127 + e) << 23);
+    inv = __int_as_float((127 - e) << 23);
 }
 
 __global__ void __launch_bounds__(kBThreads, 1)
 sketch_bf16_kernel(const float *__restrict__ At, int64_t ldat, const float *__restrict__ Bp,
                    int64_t ldbp, int64_t m, int64_t k, int64_t p, int Lfull, int C, int64_t chunk,
-                   int d, const uint32_t *__restrict__ tabA, const uint32_t *__restrict__ tabB,
-                   double *__restrict__ partial) {
+                   int d, const tab_t *__restrict__ tabA, const tab_t *__restrict__ tabB,
+                   const float *__restrict__ colmax, double *__restrict__ partial, int vec4) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __nv_bfloat16 *S = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
-    uint32_t *s_taddr = reinterpret_cast<uint32_t *>(smem_raw + kBSmem - 16);
+    int *Si = reinterpret_cast<int *>(smem_raw);
+    __nv_bfloat16 *S = reinterpret_cast<__nv_bfloat16 *>(smem_raw + kBIntBytes);
+    uint32_t *s_taddr = reinterpret_cast<uint32_t *>(smem_raw + kBIntBytes + kBBfBytes);
+    int *s_red = reinterpret_cast<int *>(smem_raw + kBIntBytes + kBBfBytes + 16);
     const int q = threadIdx.x, warp = q >> 5, lane = q & 31;
     const int g = lane >> 2, c = lane & 3;
 
@@ -254,8 +333,8 @@ sketch_bf16_kernel(const float *__restrict__ At, int64_t ldat, const float *__re
     const int64_t t1 = (t0 + chunk < k) ? t0 + chunk : k;
     const int64_t b = (int64_t)1 << Lfull;
     const int64_t slot = (int64_t)r * C + u_hi;
-    const uint32_t *tA = tabA + slot * m;
-    const uint32_t *tB = tabB + slot * p;
+    const tab_t *tA = tabA + slot * m;
+    const tab_t *tB = tabB + slot * p;
     double *out = partial + (blk * d + r) * b + (int64_t)u_hi * kBN;
 
     if (warp == 0) {
@@ -266,11 +345,12 @@ sketch_bf16_kernel(const float *__restrict__ At, int64_t ldat, const float *__re
             : "r"(smem_u32(s_taddr)), "r"(kBCols)
             : "memory");
     }
-    uint16_t *S16 = reinterpret_cast<uint16_t *>(S);
-    for (int i = q; i < kBElems; i += kBThreads) S16[i] = 0;
+    for (int i = q; i < kBN; i += kBThreads) Si[i] = 0;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int cmaxA = bf_cmax(Si, tA, m, q, s_red);
+    const int cmaxB = bf_cmax(Si, tB, p, q, s_red);
     // lanes of quadrant warp % 4; four warps share a quadrant: columns 128 * (warp / 4) ...
     const uint32_t tx = *s_taddr + ((uint32_t)(32 * (warp & 3)) << 16) + 128u * (uint32_t)(warp >> 2);
     const uint32_t tz = tx + 64;
@@ -285,13 +365,17 @@ sketch_bf16_kernel(const float *__restrict__ At, int64_t ldat, const float *__re
     }
 
     for (int64_t t = t0; t < t1; ++t) {
-        scatter_bf16(S, At + t * ldat, tA, m, q);
+        float sA, invA, sB, invB;
+        bf_scale(__ldg(colmax + t), cmaxA, sA, invA);
+        bf_scale(__ldg(colmax + k + t), cmaxB, sB, invB);
+        scatter_bf16(Si, At + t * ldat, tA, m, q, sA, vec4);
         __syncthreads();
-        bf_fwht(S, f, warp, g, c, [&](int i, const float(&vals)[8]) { tmem_st8(tx + 8 * i, vals); });
+        bf_fwht(Si, S, f, warp, g, c, invA,
+                [&](int i, const float(&vals)[8]) { tmem_st8(tx + 8 * i, vals); });
         __syncthreads();
-        scatter_bf16(S, Bp + t * ldbp, tB, p, q);
+        scatter_bf16(Si, Bp + t * ldbp, tB, p, q, sB, vec4);
         __syncthreads();
-        bf_fwht(S, f, warp, g, c, [&](int i, const float(&vals)[8]) {
+        bf_fwht(Si, S, f, warp, g, c, invB, [&](int i, const float(&vals)[8]) {
             float xs[8], zs[8];
             tmem_ld8(tx + 8 * i, xs);
             tmem_ld8(tz + 8 * i, zs);
@@ -320,10 +404,10 @@ sketch_bf16_kernel(const float *__restrict__ At, int64_t ldat, const float *__re
     }
 }
 
-// scatter words for the BF16 slice layout: padded element index | sign << 31
+// scatter words for the integer slice: word of the bucket | sign << 15
 __global__ void bf16_table_kernel(const __grid_constant__ HashParams hp, int d, int Lfull, int C,
-                                  int64_t m, int64_t p, uint32_t *__restrict__ tabA,
-                                  uint32_t *__restrict__ tabB) {
+                                  int64_t m, int64_t p, tab_t *__restrict__ tabA,
+                                  tab_t *__restrict__ tabB) {
     const int shift = 64 - Lfull;
     const int64_t nA = (int64_t)d * C * m, n = nA + (int64_t)d * C * p;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
@@ -339,7 +423,7 @@ __global__ void bf16_table_kernel(const __grid_constant__ HashParams hp, int d, 
         const uint32_t h = isA ? mas_hash(H.a1, H.c1, x, shift) : mas_hash(H.a2, H.c2, x, shift);
         const uint32_t sb = isA ? mas_sign_bit(H.as1, H.cs1, x) : mas_sign_bit(H.as2, H.cs2, x);
         const uint32_t neg = sb ^ (__popc((h >> kBL) & u_hi) & 1u);
-        const uint32_t w = (uint32_t)bf_pad((int)(h & (kBN - 1))) | (neg << 31);
+        const tab_t w = (tab_t)((uint32_t)bf_swz((int)(h & (kBN - 1))) | (neg << 15));
         if (isA)
             tabA[fidx] = w;
         else
@@ -354,8 +438,8 @@ int sketch_bf16_threads() { return kBThreads; }
 size_t sketch_bf16_smem() { return kBSmem; }
 
 cudaError_t launch_sketch_bf16(const SketchPlan &pl, const float *At, const float *Bp, int64_t m,
-                               int64_t k, int64_t p, int d, const HashParams &hp, uint32_t *tabA,
-                               uint32_t *tabB, double *partial, cudaStream_t s) {
+                               int64_t k, int64_t p, int d, const HashParams &hp, tab_t *tabA,
+                               tab_t *tabB, const float *colmax, double *partial, cudaStream_t s) {
     const int64_t n = (int64_t)d * pl.C * (m + p);
     int64_t gsz = (n + 255) / 256;
     if (gsz > 152 * 32) gsz = 152 * 32;
@@ -367,8 +451,14 @@ cudaError_t launch_sketch_bf16(const SketchPlan &pl, const float *At, const floa
                              (int)kBSmem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (int64_t)pl.nchunks * d * pl.C;
+    const bool vec4 = m % 4 == 0 && p % 4 == 0 && pl.ldat % 4 == 0 && pl.ldbp % 4 == 0 &&
+                      reinterpret_cast<uintptr_t>(At) % 16 == 0 &&
+                      reinterpret_cast<uintptr_t>(Bp) % 16 == 0 &&
+                      reinterpret_cast<uintptr_t>(tabA) % 8 == 0 &&
+                      reinterpret_cast<uintptr_t>(tabB) % 8 == 0;
     sketch_bf16_kernel<<<(unsigned)blocks, kBThreads, kBSmem, s>>>(
-        At, pl.ldat, Bp, pl.ldbp, m, k, p, pl.L, pl.C, pl.chunk, d, tabA, tabB, partial);
+        At, pl.ldat, Bp, pl.ldbp, m, k, p, pl.L, pl.C, pl.chunk, d, tabA, tabB, colmax, partial,
+        vec4 ? 1 : 0);
     return cudaGetLastError();
 }
 
