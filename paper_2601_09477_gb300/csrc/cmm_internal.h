@@ -31,6 +31,10 @@ constexpr int kMaxLloF32 = 14;   // 2^14 FP32 = 64 KiB of shared memory
 constexpr int kMaxLloF64 = 13;   // 2^13 FP64 = 64 KiB
 constexpr int kFinishLlo = 12;   // FP64 slice of the inverse transform: 2^12 doubles = 32 KiB
 
+// Most parts a sketch is split into along the inner index (the host-buffer
+// path sketches part c while part c + 1 is still being copied).
+constexpr int kMaxParts = 2;
+
 // Plan of one cmm_sketch call.
 struct SketchPlan {
     int prec;              // CMM_PREC_*
@@ -46,6 +50,12 @@ struct SketchPlan {
     bool prep_A, prep_B;   // whether A / B are converted into the workspace
     int64_t ldat, ldbp;    // leading dimensions of the operands the sketch reads
     bool tmem;             // use the TMEM variant of the FP32 kernel
+    // parts along the inner index: part c covers t in [kb[c], kb[c+1]) in
+    // pnch[c] blocks of pchunk[c]; nchunks is the total, chunk part 0's
+    int nparts;
+    int64_t kb[kMaxParts + 1];
+    int64_t pchunk[kMaxParts];
+    int pnch[kMaxParts];
 };
 
 // Plan of one cmm_backward call (mean-estimator adjoint).
@@ -125,9 +135,11 @@ size_t sketch_smem_f64(int Llo);
 // ---- extraction (extract.cu) ----
 cudaError_t launch_hash_tables(const HashParams &hp, int d, int L, int64_t m, int64_t p,
                                uint32_t *H1, uint32_t *H2, cudaStream_t s);
+// rows [0, m) of C; H1 holds each repetition's row hashes at stride ldh (pass
+// H1 + i0 and the full row count to extract rows i0 .. i0 + m - 1)
 cudaError_t launch_extract(const double *R, const uint32_t *H1, const uint32_t *H2, int d,
                            int L, int64_t m, int64_t p, int reduce, double *C, int64_t ldc,
-                           cudaStream_t s);
+                           int64_t ldh, cudaStream_t s);
 cudaError_t launch_hh_count(const double *R, const uint32_t *H1, const uint32_t *H2,
                             const double *C, int64_t ldc, int d, int L, int64_t m, int64_t p,
                             int reduce, double tau, int64_t tile, int64_t ntiles,

@@ -49,7 +49,8 @@ __global__ void __launch_bounds__(kThreads) extract_kernel(const double *__restr
                                                            const uint32_t *__restrict__ H1,
                                                            const uint32_t *__restrict__ H2, int d,
                                                            int L, int64_t m, int64_t p, int reduce,
-                                                           double *__restrict__ C, int64_t ldc) {
+                                                           double *__restrict__ C, int64_t ldc,
+                                                           int64_t ldh) {
     __shared__ uint32_t h1s[kRowsPerBlock][CMM_MAX_D];
     const int64_t b = (int64_t)1 << L;
     const uint32_t mask = (uint32_t)(b - 1);
@@ -59,7 +60,7 @@ __global__ void __launch_bounds__(kThreads) extract_kernel(const double *__restr
     const int dd = D > 0 ? D : d;
     for (int e = threadIdx.x; e < kRowsPerBlock * dd; e += kThreads) {
         const int rr = e / dd, r = e % dd;
-        h1s[rr][r] = (i0 + rr < m) ? H1[(int64_t)r * m + i0 + rr] : 0u;
+        h1s[rr][r] = (i0 + rr < m) ? H1[(int64_t)r * ldh + i0 + rr] : 0u;
     }
     __syncthreads();
     if (j >= p) return;
@@ -244,16 +245,16 @@ cudaError_t launch_hash_tables(const HashParams &hp, int d, int L, int64_t m, in
 #define CMM_ODD_D_CASES(X) X(1) X(3) X(5) X(7) X(9) X(11) X(13) X(15)
 
 cudaError_t launch_extract(const double *R, const uint32_t *H1, const uint32_t *H2, int d, int L,
-                           int64_t m, int64_t p, int reduce, double *C, int64_t ldc,
+                           int64_t m, int64_t p, int reduce, double *C, int64_t ldc, int64_t ldh,
                            cudaStream_t s) {
     const int64_t blocks = ((m + kRowsPerBlock - 1) / kRowsPerBlock) * ((p + kThreads - 1) / kThreads);
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     const unsigned g = (unsigned)blocks;
     switch (d) {
-#define X(D) case D: extract_kernel<D><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, C, ldc); break;
+#define X(D) case D: extract_kernel<D><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh); break;
         CMM_ODD_D_CASES(X)
 #undef X
-        default: extract_kernel<0><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, C, ldc);
+        default: extract_kernel<0><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh);
     }
     return cudaGetLastError();
 }

@@ -136,7 +136,7 @@ bool use_tmem_kernel() {
 
 // ---- sketch planning -------------------------------------------------------
 bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int prec, int transA,
-                 int64_t lda, int64_t ldb, SketchPlan &pl) {
+                 int64_t lda, int64_t ldb, SketchPlan &pl, int nparts = 1) {
     pl = SketchPlan{};
     pl.prec = prec;
     pl.L = L;
@@ -160,26 +160,35 @@ bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int p
     const int64_t slots = (int64_t)num_sms() * per_sm;
     const int64_t items = (int64_t)d * pl.C;
 
-    // blocks of the inner index: at most 256 t per group (bounded FP32
-    // accumulation); otherwise the count that minimises the modelled time
-    // waves * (t per group + a fixed per-CTA cost of ~2 t for the partial
-    // write-out and set-up), preferring fewer blocks on ties
-    const int64_t kk = std::max<int64_t>(k, 1);
-    const int64_t nc_min = std::max<int64_t>(1, (kk + 256 * G - 1) / (256 * G));
-    const int64_t nc_max = std::max<int64_t>(nc_min, (kk + G - 1) / G);
-    int64_t best = nc_min;
-    double best_cost = 1e300;
-    for (int64_t nc = nc_min; nc <= std::min(nc_max, nc_min + 8 * slots); ++nc) {
-        const int64_t waves = (items * nc + slots - 1) / slots;
-        const int64_t per_group = ((kk + nc - 1) / nc + G - 1) / G;
-        const double cost = (double)waves * (double)(per_group + 2);
-        if (cost < best_cost * 0.995) {
-            best_cost = cost;
-            best = nc;
+    // blocks of the inner index, per part: at most 256 t per group (bounded
+    // FP32 accumulation); otherwise the count that minimises the modelled
+    // time waves * (t per group + a fixed per-CTA cost of ~2 t for the
+    // partial write-out and set-up), preferring fewer blocks on ties
+    nparts = std::max(1, std::min(nparts, kMaxParts));
+    if (k < nparts) nparts = 1;
+    pl.nparts = nparts;
+    pl.nchunks = 0;
+    for (int c = 0; c <= nparts; ++c) pl.kb[c] = k * c / nparts;
+    for (int c = 0; c < nparts; ++c) {
+        const int64_t kk = std::max<int64_t>(pl.kb[c + 1] - pl.kb[c], 1);
+        const int64_t nc_min = std::max<int64_t>(1, (kk + 256 * G - 1) / (256 * G));
+        const int64_t nc_max = std::max<int64_t>(nc_min, (kk + G - 1) / G);
+        int64_t best = nc_min;
+        double best_cost = 1e300;
+        for (int64_t nc = nc_min; nc <= std::min(nc_max, nc_min + 8 * slots); ++nc) {
+            const int64_t waves = (items * nc + slots - 1) / slots;
+            const int64_t per_group = ((kk + nc - 1) / nc + G - 1) / G;
+            const double cost = (double)waves * (double)(per_group + 2);
+            if (cost < best_cost * 0.995) {
+                best_cost = cost;
+                best = nc;
+            }
         }
+        pl.pchunk[c] = (kk + best - 1) / best;
+        pl.pnch[c] = (int)((kk + pl.pchunk[c] - 1) / pl.pchunk[c]);
+        pl.nchunks += pl.pnch[c];
     }
-    pl.chunk = (kk + best - 1) / best;
-    pl.nchunks = (int)((kk + pl.chunk - 1) / pl.chunk);
+    pl.chunk = pl.pchunk[0];
 
     const size_t tb = f64 ? 8 : 4;
     const int tb_dtype = f64 ? CMM_F64 : CMM_F32;
@@ -252,66 +261,88 @@ ExtractWs carve_extract(void *ws, int64_t m, int64_t p, int d) {
     return e;
 }
 
+// The sketch (Compress) into R.  With nparts > 1 the inner index is split as
+// planned by plan_sketch; before part c the stream waits for ready[c] (when
+// given), so a producer on another stream may still be filling later parts.
 int run_sketch(const void *A, int64_t lda, int transA, const void *B, int64_t ldb, int dtype,
                int64_t m, int64_t k, int64_t p, const cmm_hashes *hs, int prec, double *R,
-               void *ws, cudaStream_t s) {
+               void *ws, cudaStream_t s, int nparts = 1, const cudaEvent_t *ready = nullptr) {
     SketchPlan pl;
-    plan_sketch(m, k, p, hs->d, hs->log2b, dtype, prec, transA, lda, ldb, pl);
+    plan_sketch(m, k, p, hs->d, hs->log2b, dtype, prec, transA, lda, ldb, pl, nparts);
     HashParams hp;
     fill_params(hs, hp);
     char *base = static_cast<char *>(ws);
-    const void *At = A, *Bp = B;
-    cudaError_t e;
-    if (pl.prep_A && m > 0 && k > 0) {
-        Span sp("prep_A", s);
-        e = launch_prep_A(A, lda, transA, dtype, prec, m, k, base + pl.off_At, pl.ldat, s);
-        if (e != cudaSuccess) return cuda_fail(e, "prep A");
-        At = base + pl.off_At;
-    }
-    if (pl.prep_B && p > 0 && k > 0) {
-        Span sp("prep_B", s);
-        e = launch_prep_B(B, ldb, dtype, prec, k, p, base + pl.off_Bp, pl.ldbp, s);
-        if (e != cudaSuccess) return cuda_fail(e, "prep B");
-        Bp = base + pl.off_Bp;
-    }
+    const size_t es = dtype_size(dtype);
+    const size_t tb = prec == CMM_PREC_F64 ? 8 : 4;
+    const int64_t b = int64_t(1) << hs->log2b;
+    char *At = pl.prep_A ? base + pl.off_At : (char *)const_cast<void *>(A);
+    char *Bp = pl.prep_B ? base + pl.off_Bp : (char *)const_cast<void *>(B);
     double *partial = reinterpret_cast<double *>(base + pl.off_partial);
     double *Z = reinterpret_cast<double *>(base + pl.off_Z);
-    const tab_t *tabA = reinterpret_cast<const tab_t *>(base + pl.off_tab);
-    const tab_t *tabB = tabA + (size_t)hs->d * pl.C * m;
+    tab_t *tabA = reinterpret_cast<tab_t *>(base + pl.off_tab);
+    tab_t *tabB = tabA + (size_t)hs->d * pl.C * m;
     float *colmax = reinterpret_cast<float *>(base + pl.off_colmax);
-    if (prec != CMM_PREC_F64) {
-        // the per-column scales of the fixed-point scatter
-        Span sp("colmax", s, 2);
-        e = launch_rowmax((const float *)At, pl.ldat, k, m, colmax, s);
-        if (e == cudaSuccess) e = launch_rowmax((const float *)Bp, pl.ldbp, k, p, colmax + k, s);
-        if (e != cudaSuccess) return cuda_fail(e, "column maxima");
-    }
+    cudaError_t e;
     if (pl.tmem) {
-        {
-            Span sp("sketch_tables", s);
-            e = launch_sketch_tm_tables(pl, m, p, hs->d, hp, const_cast<tab_t *>(tabA),
-                                        const_cast<tab_t *>(tabB), s);
-        }
+        Span sp("sketch_tables", s);
+        e = launch_sketch_tm_tables(pl, m, p, hs->d, hp, tabA, tabB, s);
         if (e != cudaSuccess) return cuda_fail(e, "scatter tables");
-        Span sp("sketch_f32", s);
-        e = launch_sketch_tm(pl, (const float *)At, (const float *)Bp, m, k, p, hs->d, tabA, tabB,
-                             colmax, partial, s);
-    } else {
-        // these launchers build their scatter tables first (two launches)
-        Span sp(prec == CMM_PREC_F64 ? "sketch_f64"
-                : prec == CMM_PREC_BF16TC ? "sketch_bf16tc" : "sketch_f32", s, 2);
-        if (prec == CMM_PREC_F64)
-            e = launch_sketch_f64(pl, (const double *)At, (const double *)Bp, m, k, p, hs->d, hp,
-                                  tabA, tabB, nullptr, partial, s);
-        else if (prec == CMM_PREC_BF16TC)
-            e = launch_sketch_bf16(pl, (const float *)At, (const float *)Bp, m, k, p, hs->d, hp,
-                                   const_cast<tab_t *>(tabA), const_cast<tab_t *>(tabB), colmax,
-                                   partial, s);
-        else
-            e = launch_sketch_f32(pl, (const float *)At, (const float *)Bp, m, k, p, hs->d, hp,
-                                  tabA, tabB, colmax, partial, s);
     }
-    if (e != cudaSuccess) return cuda_fail(e, "sketch kernel");
+    int64_t blk0 = 0;
+    for (int c = 0; c < pl.nparts; ++c) {
+        const int64_t k0 = pl.kb[c], kp = pl.kb[c + 1] - pl.kb[c];
+        if (ready && ready[c]) {
+            e = cudaStreamWaitEvent(s, ready[c], 0);
+            if (e != cudaSuccess) return cuda_fail(e, "wait for operand part");
+        }
+        if (pl.prep_A && m > 0 && kp > 0) {
+            Span sp("prep_A", s);
+            // columns k0.. of A, or rows k0.. of A^T
+            const char *Ap = static_cast<const char *>(A) + (transA ? k0 * lda : k0) * es;
+            e = launch_prep_A(Ap, lda, transA, dtype, prec, m, kp, At + k0 * pl.ldat * tb, pl.ldat, s);
+            if (e != cudaSuccess) return cuda_fail(e, "prep A");
+        }
+        if (pl.prep_B && p > 0 && kp > 0) {
+            Span sp("prep_B", s);
+            e = launch_prep_B(static_cast<const char *>(B) + k0 * ldb * es, ldb, dtype, prec, kp, p,
+                              Bp + k0 * pl.ldbp * tb, pl.ldbp, s);
+            if (e != cudaSuccess) return cuda_fail(e, "prep B");
+        }
+        const char *Atc = At + k0 * pl.ldat * tb;
+        const char *Bpc = Bp + k0 * pl.ldbp * tb;
+        float *cm = colmax + 2 * k0;   // this part's maxima: A^T rows, then B rows
+        if (prec != CMM_PREC_F64) {
+            // the per-column scales of the fixed-point scatter
+            Span sp("colmax", s, 2);
+            e = launch_rowmax((const float *)Atc, pl.ldat, kp, m, cm, s);
+            if (e == cudaSuccess) e = launch_rowmax((const float *)Bpc, pl.ldbp, kp, p, cm + kp, s);
+            if (e != cudaSuccess) return cuda_fail(e, "column maxima");
+        }
+        SketchPlan pp = pl;   // this part's blocks
+        pp.chunk = pl.pchunk[c];
+        pp.nchunks = pl.pnch[c];
+        double *pc = partial + blk0 * hs->d * b;
+        blk0 += pl.pnch[c];
+        if (pl.tmem) {
+            Span sp("sketch_f32", s);
+            e = launch_sketch_tm(pp, (const float *)Atc, (const float *)Bpc, m, kp, p, hs->d, tabA,
+                                 tabB, cm, pc, s);
+        } else {
+            // these launchers build their scatter tables first (two launches)
+            Span sp(prec == CMM_PREC_F64 ? "sketch_f64"
+                    : prec == CMM_PREC_BF16TC ? "sketch_bf16tc" : "sketch_f32", s, 2);
+            if (prec == CMM_PREC_F64)
+                e = launch_sketch_f64(pp, (const double *)Atc, (const double *)Bpc, m, kp, p,
+                                      hs->d, hp, tabA, tabB, nullptr, pc, s);
+            else if (prec == CMM_PREC_BF16TC)
+                e = launch_sketch_bf16(pp, (const float *)Atc, (const float *)Bpc, m, kp, p, hs->d,
+                                       hp, tabA, tabB, cm, pc, s);
+            else
+                e = launch_sketch_f32(pp, (const float *)Atc, (const float *)Bpc, m, kp, p, hs->d,
+                                      hp, tabA, tabB, cm, pc, s);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "sketch kernel");
+    }
     {
         Span sp("finish", s, 2);
         e = launch_finish(partial, pl.nchunks, hs->d, hs->log2b, Z, R, s);
@@ -334,7 +365,7 @@ int run_extract(const double *R, const cmm_hashes *hs, int64_t m, int64_t p, int
     if (e != cudaSuccess) return cuda_fail(e, "hash tables");
     {
         Span sp("extract", s);
-        e = launch_extract(R, ew.H1, ew.H2, hs->d, hs->log2b, m, p, reduce, C, ldc, s);
+        e = launch_extract(R, ew.H1, ew.H2, hs->d, hs->log2b, m, p, reduce, C, ldc, m, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "extract kernel");
     return CMM_OK;
@@ -646,15 +677,78 @@ int cmm_multiply(const void *A, int64_t lda, int32_t transA, const void *B, int6
     return run_extract(Rw, hs, m, p, reduce, C, ldc, scratch, s);
 }
 
+namespace {
+
+// ---- the host-buffer path: copies overlapped with the computation ----------
+// The inner index is split in two parts when the operands are large: part 1
+// is copied to the device on an internal copy stream while part 0 is
+// prepared and sketched on the caller's stream.  The estimate is extracted in
+// row blocks, each copied back while the next is extracted.
+constexpr int kHostRowBlocks = 4;
+
+int host_parts(int64_t m, int64_t k, int64_t p, size_t es) {
+    return (k >= 512 && (double)(m + p) * (double)k * (double)es >= 64.0 * 1048576.0) ? 2 : 1;
+}
+
+int host_row_blocks(int64_t m, int64_t p) {
+    return (m >= 4 * 256 && (double)m * (double)p * 8.0 >= 32.0 * 1048576.0) ? kHostRowBlocks : 1;
+}
+
+size_t host_sketch_ws(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int prec,
+                      int transA) {
+    SketchPlan pl;
+    if (!plan_sketch(m, k, p, d, L, dtype, prec, transA, transA ? m : k, p, pl,
+                     host_parts(m, k, p, dtype_size(dtype))))
+        return 0;
+    return pl.total;
+}
+
+// per device: one copy stream and its events, created on first use; a call
+// holds the device's mutex for its whole duration (calls from several host
+// threads on one device run one after the other)
+constexpr int kMaxDevices = 64;
+constexpr int kCopyEvents = 4 + kMaxParts + kHostRowBlocks;
+struct CopyCtx {
+    std::mutex mu;
+    bool ready = false;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev[kCopyEvents] = {};
+};
+CopyCtx g_copy[kMaxDevices];
+
+int copy_ctx(CopyCtx *&out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(CMM_ERR_RANGE, "device index %d out of range", dev);
+    out = &g_copy[dev];
+    return CMM_OK;
+}
+
+int copy_ctx_init(CopyCtx &c) {
+    if (c.ready) return CMM_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&c.cs, cudaStreamNonBlocking);
+    for (int i = 0; e == cudaSuccess && i < kCopyEvents; ++i)
+        e = cudaEventCreateWithFlags(&c.ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "copy stream set-up");
+    c.ready = true;
+    return CMM_OK;
+}
+
+}  // namespace
+
 size_t cmm_multiply_host_workspace_bytes(int64_t m, int64_t k, int64_t p, int32_t d,
                                          int32_t log2b, int32_t dtype, int32_t prec,
                                          int32_t transA, int64_t capacity) {
     const size_t mw = cmm_multiply_workspace_bytes(m, k, p, d, log2b, dtype, prec, transA);
     if (!mw || capacity < 0) return 0;
+    const size_t sk = host_sketch_ws(m, k, p, d, log2b, dtype, prec, transA);
+    const size_t ex = extract_ws_bytes(m, p, d);
     const size_t es = dtype_size(dtype);
     return align_up((size_t)m * k * es) + align_up((size_t)k * p * es) +
            align_up((size_t)m * p * sizeof(double)) +
-           align_up((size_t)capacity * (2 * sizeof(int32_t) + sizeof(double))) + mw;
+           align_up((size_t)capacity * (2 * sizeof(int32_t) + sizeof(double))) +
+           align_up((size_t)d * (size_t(1) << log2b) * sizeof(double)) + std::max(sk, ex);
 }
 
 int cmm_multiply_host(const void *A, int64_t lda, int32_t transA, const void *B, int64_t ldb,
@@ -678,7 +772,16 @@ int cmm_multiply_host(const void *A, int64_t lda, int32_t transA, const void *B,
                                                           transA, cap);
     rc = check_ws(ws, ws_bytes, need);
     if (rc) return rc;
+    CopyCtx *cx = nullptr;
+    rc = copy_ctx(cx);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(cx->mu);
+    rc = copy_ctx_init(*cx);
+    if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaStream_t cs = cx->cs;
+    cudaEvent_t ev_start = cx->ev[0], ev_done = cx->ev[1];
+    cudaEvent_t *ev_in = cx->ev + 4, *ev_out = cx->ev + 4 + kMaxParts;
     const size_t es = dtype_size(dtype);
     char *base = static_cast<char *>(ws);
     char *dA = base;
@@ -691,33 +794,75 @@ int cmm_multiply_host(const void *A, int64_t lda, int32_t transA, const void *B,
     int32_t *dJ = dI + cap;
     double *dV = reinterpret_cast<double *>(base + align_up((size_t)cap * 2 * sizeof(int32_t)));
     base += align_up((size_t)cap * (2 * sizeof(int32_t) + sizeof(double)));
-    // A as stored: m x k (transA = 0) or k x m (transA = 1), compacted on the device
-    const int64_t arows = transA ? k : m, acols = transA ? m : k;
-    cudaError_t e;
-    if (arows > 0 && acols > 0) {
-        Span sp("h2d_A", s, 0);
-        e = cudaMemcpy2DAsync(dA, acols * es, A, lda * es, acols * es, arows,
-                              cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return cuda_fail(e, "copy A to device");
-    }
-    if (k > 0 && p > 0) {
-        Span sp("h2d_B", s, 0);
-        e = cudaMemcpy2DAsync(dB, p * es, B, ldb * es, p * es, k, cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return cuda_fail(e, "copy B to device");
-    }
     const size_t rbytes = align_up((size_t)hs->d * (size_t(1) << hs->log2b) * sizeof(double));
     double *Rw = reinterpret_cast<double *>(base);
     void *scratch = base + rbytes;
-    rc = run_sketch(dA, acols > 0 ? acols : 1, transA, dB, p > 0 ? p : 1, dtype, m, k, p, hs, prec,
-                    Rw, scratch, s);
+
+    // the copy stream starts after the work already queued on the caller's stream
+    cudaError_t e = cudaEventRecord(ev_start, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_start, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "copy stream ordering");
+    // operands, part by part (A as stored: m x k, or k x m when transA; the
+    // device copy is compact)
+    SketchPlan pl;
+    const int nparts = host_parts(m, k, p, es);
+    plan_sketch(m, k, p, hs->d, hs->log2b, dtype, prec, transA, transA ? m : k, p, pl, nparts);
+    const int64_t acols = transA ? m : k;
+    for (int c = 0; c < pl.nparts; ++c) {
+        const int64_t k0 = pl.kb[c], kp = pl.kb[c + 1] - pl.kb[c];
+        if (m > 0 && kp > 0) {
+            Span sp("h2d_A", cs, 0);
+            if (transA)
+                e = cudaMemcpy2DAsync(dA + k0 * m * es, m * es, static_cast<const char *>(A) + k0 * lda * es,
+                                      lda * es, m * es, kp, cudaMemcpyHostToDevice, cs);
+            else
+                e = cudaMemcpy2DAsync(dA + k0 * es, k * es, static_cast<const char *>(A) + k0 * es,
+                                      lda * es, kp * es, m, cudaMemcpyHostToDevice, cs);
+            if (e != cudaSuccess) return cuda_fail(e, "copy A to device");
+        }
+        if (kp > 0 && p > 0) {
+            Span sp("h2d_B", cs, 0);
+            e = cudaMemcpy2DAsync(dB + k0 * p * es, p * es, static_cast<const char *>(B) + k0 * ldb * es,
+                                  ldb * es, p * es, kp, cudaMemcpyHostToDevice, cs);
+            if (e != cudaSuccess) return cuda_fail(e, "copy B to device");
+        }
+        e = cudaEventRecord(ev_in[c], cs);
+        if (e != cudaSuccess) return cuda_fail(e, "operand part event");
+    }
+    rc = run_sketch(dA, acols > 0 ? acols : 1, transA, dB, p > 0 ? p : 1, dtype, m, k, p, hs,
+                    prec, Rw, scratch, s, pl.nparts, ev_in);
     if (rc) return rc;
-    rc = run_extract(Rw, hs, m, p, reduce, dC, p, scratch, s);
-    if (rc) return rc;
-    if (C && m > 0 && p > 0) {
-        Span sp("d2h_C", s, 0);
-        e = cudaMemcpy2DAsync(C, ldc * sizeof(double), dC, p * sizeof(double), p * sizeof(double),
-                              m, cudaMemcpyDeviceToHost, s);
-        if (e != cudaSuccess) return cuda_fail(e, "copy C to host");
+    // the estimate in row blocks, each copied back while the next is extracted
+    if (m > 0 && p > 0) {
+        HashParams hp;
+        fill_params(hs, hp);
+        ExtractWs ew = carve_extract(scratch, m, p, hs->d);
+        {
+            Span sp("hash_tables", s);
+            e = launch_hash_tables(hp, hs->d, hs->log2b, m, p, ew.H1, ew.H2, s);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "hash tables");
+        const int nrb = host_row_blocks(m, p);
+        for (int i = 0; i < nrb; ++i) {
+            const int64_t i0 = m * i / nrb, mb = m * (i + 1) / nrb - i0;
+            if (mb == 0) continue;
+            {
+                Span sp("extract", s);
+                e = launch_extract(Rw, ew.H1 + i0, ew.H2, hs->d, hs->log2b, mb, p, reduce,
+                                   dC + i0 * p, p, m, s);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "extract kernel");
+            if (C) {
+                e = cudaEventRecord(ev_out[i], s);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_out[i], 0);
+                if (e != cudaSuccess) return cuda_fail(e, "row block event");
+                Span sp("d2h_C", cs, 0);
+                e = cudaMemcpy2DAsync(C + i0 * ldc, ldc * sizeof(double), dC + i0 * p,
+                                      p * sizeof(double), p * sizeof(double), mb,
+                                      cudaMemcpyDeviceToHost, cs);
+                if (e != cudaSuccess) return cuda_fail(e, "copy C to host");
+            }
+        }
     }
     int hh_rc = CMM_OK;
     if (count) {
@@ -735,7 +880,10 @@ int cmm_multiply_host(const void *A, int64_t lda, int32_t transA, const void *B,
             if (e != cudaSuccess) return cuda_fail(e, "copy heavy hitters to host");
         }
     }
-    e = cudaStreamSynchronize(s);
+    // the caller's stream ends after the last copy
+    e = cudaEventRecord(ev_done, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_done, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "multiply_host sync");
     if (hh_rc == CMM_ERR_CAPACITY)
         return fail(CMM_ERR_CAPACITY, "%lld heavy hitters, capacity %lld", (long long)*count,

@@ -1,0 +1,70 @@
+"""The host-buffer entry point (cmm_multiply_host): operands copied in parts on
+an internal stream while earlier parts are sketched, the estimate extracted in
+row blocks and copied back block by block.  Its results must equal those of
+the device-buffer path (cmm_multiply + cmm_threshold): bit for bit on +-1
+inputs, where every quantity is an integer and the order of additions cannot
+matter, and bit for bit whenever the operands are too small to be split."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cmm():
+    assert torch.cuda.is_available(), "these tests need a CUDA GPU"
+    from paper_2601_09477_gb300 import cmm as mod
+    return mod
+
+
+def _pm1(shape, seed):
+    g = np.random.default_rng(seed)
+    return np.where(g.random(shape) < 0.5, -1.0, 1.0)
+
+
+@pytest.mark.parametrize("transA", [False, True])
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_host_path_split_matches_device_path(cmm, transA, prec):
+    # 2048^3 FP64: 64 MiB of operands (split in two parts along the inner
+    # index) and a 32 MiB estimate (four row blocks)
+    n = 2048
+    A = _pm1((n, n), 1)
+    A[5] = A[9]            # a planted pair: C[5, 9] = n
+    B = A.T.copy()
+    h = cmm.make_hashes(17, 9, 16)
+    Ah = torch.from_numpy(np.ascontiguousarray(A.T) if transA else A).pin_memory()
+    Bh = torch.from_numpy(B).pin_memory()
+    tau = 0.75 * n
+    Ch, (I, J, V) = cmm.multiply_host(Ah, Bh, h, prec=prec, transA=transA, tau=tau,
+                                      capacity=1 << 20)
+    Cd = cmm.multiply(Ah.cuda(), Bh.cuda(), h, prec=prec, transA=transA)
+    assert torch.equal(Ch, Cd.cpu())
+    Id, Jd, Vd = cmm.threshold(Cd, tau, capacity=1 << 20)
+    assert np.array_equal(I.numpy(), Id.cpu().numpy())
+    assert np.array_equal(J.numpy(), Jd.cpu().numpy())
+    assert np.array_equal(V.numpy(), Vd.cpu().numpy())
+    assert (5, 9) in set(zip(I.tolist(), J.tolist()))
+
+
+def test_host_path_padded_small(cmm):
+    # below the split thresholds: one part, one row block; padded leading
+    # dimensions on the host side
+    m, k, p, L, d = 300, 200, 250, 12, 3
+    g = np.random.default_rng(3)
+    Abig = torch.from_numpy(g.standard_normal((m, k + 7)).astype(np.float32)).pin_memory()
+    Bbig = torch.from_numpy(g.standard_normal((k, p + 3)).astype(np.float32)).pin_memory()
+    A, B = Abig[:, :k], Bbig[:, :p]
+    h = cmm.make_hashes(5, d, L)
+    Ch, _ = cmm.multiply_host(A, B, h, prec="f32", tau=1e30, capacity=4)
+    Cd = cmm.multiply(A.cuda(), B.cuda(), h, prec="f32")
+    assert torch.equal(Ch, Cd.cpu())
+    # and the estimate is the oracle's decompression of the oracle's sketch
+    A64 = A.double().numpy()
+    B64 = B.double().numpy()
+    Ro = orc.compress(A64, B64, h.params, L, nthreads=8)
+    R = cmm.sketch(A.cuda(), B.cuda(), h, prec="f32").cpu().numpy()
+    scale = float(np.sum(np.linalg.norm(A64, axis=0) * np.linalg.norm(B64, axis=1)))
+    assert np.abs(R - Ro).max() / scale <= 1e-5
