@@ -26,11 +26,10 @@ def _pm1(shape, seed):
 
 
 @pytest.mark.parametrize("transA", [False, True])
-@pytest.mark.parametrize("prec", ["f32", "f64"])
-def test_host_path_split_matches_device_path(cmm, transA, prec):
-    # 2048^3 FP64: 64 MiB of operands (split in two parts along the inner
-    # index) and a 32 MiB estimate (four row blocks)
-    n = 2048
+@pytest.mark.parametrize("n,prec", [(2048, "f32"), (2048, "f64"), (4096, "f32")])
+def test_host_path_split_matches_device_path(cmm, transA, n, prec):
+    # FP64 operands of 64 MiB or more: two parts along the inner index;
+    # estimates of 32 MiB or more: four row blocks
     A = _pm1((n, n), 1)
     A[5] = A[9]            # a planted pair: C[5, 9] = n
     B = A.T.copy()
