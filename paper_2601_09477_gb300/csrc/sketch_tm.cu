@@ -201,11 +201,24 @@ __device__ __forceinline__ void scatter_fixed(int *Si, const float *__restrict__
 #pragma unroll
         for (int e = 0; e < B; ++e) scatter_one(Si, w[e], val[e], __float_as_uint(s));
     }
-    for (; i < n; i += kTmP) scatter_one(Si, __ldg(tab + i), ld_stream(col + i), __float_as_uint(s));
+    if (i < n) {   // the last, partial batch: all loads first
+        float val[B];
+        tab_t w[B];
+#pragma unroll
+        for (int e = 0; e < B; ++e) {
+            const bool ok = i + e * (int64_t)kTmP < n;
+            val[e] = ok ? ld_stream(col + i + e * (int64_t)kTmP) : 0.f;
+            w[e] = ok ? __ldg(tab + i + e * (int64_t)kTmP) : (tab_t)0;
+        }
+#pragma unroll
+        for (int e = 0; e < B; ++e)
+            if (i + e * (int64_t)kTmP < n) scatter_one(Si, w[e], val[e], __float_as_uint(s));
+    }
 }
 
 // vectorised variant: n % 4 == 0, col 16-byte and tab 8-byte aligned; thread
-// q takes elements 4i .. 4i+3 for i = q, q + 128, ...
+// q takes elements 4i .. 4i+3 for i = q, q + 128, ...; batches of BV float4
+// with all their loads issued before the atomics
 template <int BV>
 __device__ __forceinline__ void scatter_fixed_v4(int *Si, const float *__restrict__ col,
                                                  const tab_t *__restrict__ tab, int64_t n, int q,
@@ -231,13 +244,24 @@ __device__ __forceinline__ void scatter_fixed_v4(int *Si, const float *__restric
             scatter_one(Si, w[e].y >> 16, val[e].w, sb);
         }
     }
-    for (; i < n4; i += kTmP) {
-        const float4 v = __ldcs(c4 + i);
-        const uint2 w = __ldg(t4 + i);
-        scatter_one(Si, w.x & 0xffffu, v.x, sb);
-        scatter_one(Si, w.x >> 16, v.y, sb);
-        scatter_one(Si, w.y & 0xffffu, v.z, sb);
-        scatter_one(Si, w.y >> 16, v.w, sb);
+    if (i < n4) {   // the last, partial batch: loads guarded, still all issued first
+        float4 val[BV];
+        uint2 w[BV];
+#pragma unroll
+        for (int e = 0; e < BV; ++e) {
+            const bool ok = i + e * (int64_t)kTmP < n4;
+            val[e] = ok ? __ldcs(c4 + i + e * (int64_t)kTmP) : make_float4(0.f, 0.f, 0.f, 0.f);
+            w[e] = ok ? __ldg(t4 + i + e * (int64_t)kTmP) : make_uint2(0u, 0u);
+        }
+#pragma unroll
+        for (int e = 0; e < BV; ++e) {
+            if (i + e * (int64_t)kTmP < n4) {
+                scatter_one(Si, w[e].x & 0xffffu, val[e].x, sb);
+                scatter_one(Si, w[e].x >> 16, val[e].y, sb);
+                scatter_one(Si, w[e].y & 0xffffu, val[e].z, sb);
+                scatter_one(Si, w[e].y >> 16, val[e].w, sb);
+            }
+        }
     }
 }
 
