@@ -278,7 +278,8 @@ def run_cmm(a):
     try:
         with open(TRAFFIC_PATH) as f:
             tj = json.load(f)
-        if tj.get("source_hash") == source_hash() and tj.get("n") == n and tj.get("log2b") == L:
+        if (a.prec == "f32" and tj.get("source_hash") == source_hash() and tj.get("n") == n
+                and tj.get("log2b") == L):
             traffic = tj.get("dram_bytes_per_launch")
     except Exception:
         pass
