@@ -4,11 +4,13 @@ TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU
 baseline leg use this module; the library never does.  It shares no code with
 the CUDA library -- it compiles and loads its own C file with gcc.
 
-Every function here is a thin ctypes wrapper; the arithmetic lives in
-``cmm_oracle.c`` and follows Algorithm 1 (Compress / Decompress) of
+The XOR (FWHT) form: every function is a thin ctypes wrapper; the arithmetic
+lives in ``cmm_oracle.c`` and follows Algorithm 1 (Compress / Decompress) of
 Andersson & Karppa, "Engineering Compressed Matrix Multiplication with the
 Fast Walsh-Hadamard Transform" (arXiv 2601.09477), with the hash family of
-Sec. 4.2.  See that file's header for the definitions and readings.
+Sec. 4.2.  See that file's header for the definitions and readings.  The
+cyclic (FFT) form of Sec. 3.1 at the end of this file is plain numpy on the
+same hash values.
 """
 from __future__ import annotations
 
@@ -253,3 +255,69 @@ def adjoint(A, B, hp: np.ndarray, log2b: int, I, J, W, transA: bool = False):
     dA = M @ B.T
     dB = Am.T @ M
     return (dA.T.copy() if transA else dA), dB
+
+
+# ---- Pagh's original (cyclic) form, Sec. 3.1 ----------------------------------
+# Same sketches x_t, y_t as Algorithm 1 (hashes of Sec. 4.2), but the product
+# polynomial is the cyclic convolution of Sec. 2, (x * y)[w] = sum over
+# u + v = w mod b of x[u] y[v], taken here through numpy's FFT (FP64, a library
+# step), and the estimate reads bucket (h1(i) + h2(j)) mod b.
+
+def _hash_arrays(hp_r, m: int, p: int, log2b: int):
+    h1 = buckets(int(hp_r[0]), int(hp_r[1]), m, log2b)
+    h2 = buckets(int(hp_r[2]), int(hp_r[3]), p, log2b)
+    s1 = signs(int(hp_r[4]), int(hp_r[5]), m).astype(np.float64)
+    s2 = signs(int(hp_r[6]), int(hp_r[7]), p).astype(np.float64)
+    return h1.astype(np.int64), h2.astype(np.int64), s1, s2
+
+
+def compress_cyclic(A, B, hp: np.ndarray, log2b: int, transA: bool = False) -> np.ndarray:
+    """R (d x b): R_r = sum_t x_{r,t} * y_{r,t} (cyclic convolution), FP64."""
+    A = _f64(A)
+    B = _f64(B)
+    Am = A.T if transA else A            # m x k
+    m, k = Am.shape
+    p = B.shape[1]
+    b = 1 << log2b
+    hp = np.ascontiguousarray(hp, dtype=np.uint64)
+    R = np.zeros((hp.shape[0], b), dtype=np.float64)
+    for r in range(hp.shape[0]):
+        h1, h2, s1, s2 = _hash_arrays(hp[r], m, p, log2b)
+        X = np.zeros((b, k))
+        np.add.at(X, h1, s1[:, None] * Am)          # column t of X is x_t
+        Y = np.zeros((b, k))
+        np.add.at(Y, h2, s2[:, None] * B.T)         # column t of Y is y_t
+        P = (np.fft.fft(X, axis=0) * np.fft.fft(Y, axis=0)).sum(axis=1)
+        R[r] = np.real(np.fft.ifft(P))
+    return R
+
+
+def R_entry_cyclic(A, B, hp: np.ndarray, log2b: int, r: int, w: int,
+                   transA: bool = False) -> float:
+    """R_r[w] from the bucket definition: sum of s1(i) s2(j) C[i, j] over every
+    (i, j) with h1(i) + h2(j) = w (mod b), C = A B."""
+    A = _f64(A)
+    B = _f64(B)
+    Am = A.T if transA else A
+    m, p = Am.shape[0], B.shape[1]
+    h1, h2, s1, s2 = _hash_arrays(np.ascontiguousarray(hp, dtype=np.uint64)[r], m, p, log2b)
+    C = Am @ B
+    sel = ((h1[:, None] + h2[None, :]) % (1 << log2b)) == w
+    return float(np.sum((s1[:, None] * s2[None, :] * C)[sel]))
+
+
+def extract_cyclic(R: np.ndarray, hp: np.ndarray, m: int, p: int, reduce: int = MEDIAN,
+                   rows=None) -> np.ndarray:
+    """Estimate rows ``rows=(i0, i1)``: median (or mean) over r of
+    s1(i) s2(j) R_r[(h1(i) + h2(j)) mod b]; even d: mean of the two middle values."""
+    R = _f64(R)
+    hp = np.ascontiguousarray(hp, dtype=np.uint64)
+    d, b = R.shape
+    L = b.bit_length() - 1
+    i0, i1 = rows if rows is not None else (0, m)
+    vals = np.empty((d, i1 - i0, p))
+    for r in range(d):
+        h1, h2, s1, s2 = _hash_arrays(hp[r], m, p, L)
+        w = (h1[i0:i1, None] + h2[None, :]) % b
+        vals[r] = s1[i0:i1, None] * s2[None, :] * R[r][w]
+    return vals.mean(axis=0) if reduce == MEAN else np.median(vals, axis=0)

@@ -307,6 +307,101 @@ def test_unbiased_and_variance_bound():
         assert est[:, q].var() <= 1.1 * bound
 
 
+# ---------------------------------------------------------------- cyclic form
+# Pagh's original (Sec. 3.1): bucket h1(i) + h2(j) mod b, products through the
+# cyclic convolution of Sec. 2.  The oracle takes it through numpy's FFT; these
+# pins check it against loops that use neither the FFT nor the oracle's scatter.
+
+def _sketch_loops(col, a, c, sa, sc, L):
+    # x[u] = sum over i with h(i) = u of s(i) col[i], element by element
+    x = [0.0] * (1 << L)
+    for i, v in enumerate(col):
+        x[orc.bucket(a, c, i, L)] += orc.sign(sa, sc, i) * v
+    return x
+
+
+def test_cyclic_matches_brute_force_convolution():
+    g = np.random.default_rng(41)
+    m, k, p, L, d = 37, 4, 29, 4, 2
+    A = g.standard_normal((m, k))
+    B = g.standard_normal((k, p))
+    hp = orc.draw_hashes(77, d)
+    R = orc.compress_cyclic(A, B, hp, L)
+    b = 1 << L
+    for r in range(d):
+        a1, c1, a2, c2, as1, cs1, as2, cs2 = (int(v) for v in hp[r])
+        want = [0.0] * b
+        for t in range(k):
+            x = _sketch_loops(A[:, t], a1, c1, as1, cs1, L)
+            y = _sketch_loops(B[t, :], a2, c2, as2, cs2, L)
+            for u in range(b):
+                for v in range(b):
+                    want[(u + v) % b] += x[u] * y[v]
+        np.testing.assert_allclose(R[r], want, rtol=0, atol=1e-12)
+
+
+def test_cyclic_bucket_identity_and_pm1_integers():
+    # R_r[w] = sum of s1(i) s2(j) C[i, j] over h1(i) + h2(j) = w (mod b); on +-1
+    # inputs every R value is an integer
+    g = np.random.default_rng(43)
+    m, k, p, L = 9, 6, 8, 3
+    A = np.where(g.random((m, k)) < 0.5, -1.0, 1.0)
+    B = np.where(g.random((k, p)) < 0.5, -1.0, 1.0)
+    hp = orc.draw_hashes(5, 2)
+    R = orc.compress_cyclic(A, B, hp, L)
+    b = 1 << L
+    for r in range(2):
+        a1, c1, a2, c2, as1, cs1, as2, cs2 = (int(v) for v in hp[r])
+        want = [0] * b
+        for i in range(m):
+            for j in range(p):
+                cij = sum(int(A[i, t]) * int(B[t, j]) for t in range(k))
+                w = (orc.bucket(a1, c1, i, L) + orc.bucket(a2, c2, j, L)) % b
+                want[w] += orc.sign(as1, cs1, i) * orc.sign(as2, cs2, j) * cij
+        np.testing.assert_allclose(R[r], want, rtol=0, atol=1e-9)
+        assert np.abs(R[r] - np.round(R[r])).max() < 1e-9
+
+
+def test_cyclic_exact_recovery_of_sparse_product():
+    # the n = 256 case with cyclic buckets: S recovered except where collisions
+    # hit a majority of repetitions
+    A, B, S = wl.orthogonal_sparse(seed=1001)
+    hp = orc.draw_hashes(2001, 5)
+    R = orc.compress_cyclic(A, B, hp, 12)
+    C = orc.extract_cyclic(R, hp, 256, 256)
+    err = np.abs(C - S)
+    assert np.mean(err < 1e-9) > 0.999
+    nz = list(zip(*np.nonzero(S)))
+    for (i, j) in zip(*np.nonzero(err >= 1e-9)):
+        hits = 0
+        for r in range(5):
+            a1, c1, a2, c2 = (int(v) for v in hp[r, :4])
+            w = (orc.bucket(a1, c1, int(i), 12) + orc.bucket(a2, c2, int(j), 12)) % 4096
+            hits += any((orc.bucket(a1, c1, int(u), 12) + orc.bucket(a2, c2, int(v), 12)) % 4096 == w
+                        for (u, v) in nz if (u, v) != (i, j))
+        assert hits >= 3
+
+
+def test_cyclic_unbiased_and_variance_bound():
+    # d = 1: E[Chat_ij] = C_ij and Var <= ||C||_F^2 / b hold for the cyclic form
+    # too (Sec. 3.1; Pagh's Theorem 3.1)
+    g = np.random.default_rng(37)
+    n, L, S = 20, 4, 2000
+    A = g.standard_normal((n, n))
+    B = g.standard_normal((n, n))
+    C = A @ B
+    pairs = [(0, 0), (4, 9), (19, 2)]
+    est = np.empty((S, len(pairs)))
+    for s in range(S):
+        hp = orc.draw_hashes(20_000 + s, 1)
+        Cs = orc.extract_cyclic(orc.compress_cyclic(A, B, hp, L), hp, n, n)
+        est[s] = [Cs[i, j] for (i, j) in pairs]
+    bound = (C ** 2).sum() / (1 << L)
+    for q, (i, j) in enumerate(pairs):
+        assert abs(est[:, q].mean() - C[i, j]) < 5.0 * math.sqrt(bound / S)
+        assert est[:, q].var() <= 1.1 * bound
+
+
 # ---------------------------------------------------------------- adjoint
 
 def _loss(A, B, hp, L, I, J, W):
