@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--workload", default="planted",
-                    choices=["planted", "batched", "precision", "diff"],
+                    choices=["planted", "batched", "precision", "diff", "cyclic"],
                     help="planted (the headline line) or one of the other configurations")
     ap.add_argument("--tune-budget", type=float, default=120.0)
     return ap.parse_args()
@@ -501,6 +501,50 @@ def run_diff(a):
     return 0
 
 
+def run_cyclic(a):
+    """FWHT form (Algorithm 1) vs Pagh's cyclic FFT form (Sec. 3.1) on the same
+    problem: multiply ms of each and their ratio (the paper's FFT / FWHT speedup
+    SU3), with the per-kernel trace and the planted-pair recall of each."""
+    import torch
+    from paper_2601_09477_gb300 import cmm
+    from paper_2601_09477_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    n, L, d = a.n, a.log2b, a.d
+    A, B, pairs = wl.gpu_planted_pm1(n, 64, 0.9, 1002, "cuda", torch.float32)
+    h = cmm.make_hashes(2002, d, L)
+    ws = torch.empty(max(cmm.multiply_workspace_bytes(n, n, n, h, torch.float32, "f32"),
+                         int(cmm.lib.cmm_multiply_cyclic_workspace_bytes(n, n, n, d, L, 1, 1, 0))),
+                     dtype=torch.uint8, device="cuda")
+    C = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    forms = {"fwht": lambda: cmm.multiply(A, B, h, prec="f32", out=C, ws=ws),
+             "cyclic": lambda: cmm.multiply_cyclic(A, B, h, out=C, ws=ws)}
+    times, kernels, recall = {}, {}, {}
+    tau = 0.5 * n
+    pl = pairs.tolist()
+    planted = {(int(i), int(j)) for i, j in pl} | {(int(j), int(i)) for i, j in pl}
+    for name, fn in forms.items():
+        for _ in range(a.warmup):
+            fn()
+        torch.cuda.synchronize()
+        cmm.trace_enable(True)
+        times[name] = round(_events_ms(fn, a.steps), 3)
+        cmm.trace_enable(False)
+        kernels[name] = {k: round(v[1] / a.steps, 4) for k, v in cmm.trace_read().items()}
+        I, J, _ = cmm.threshold(C, tau)
+        found = set(zip(I.tolist(), J.tolist()))
+        recall[name] = sum(1 for q in planted if q in found) / len(planted)
+    res = {"metric": "FWHT vs cyclic FFT form: multiply ms (sketch + finish + extraction) and "
+                     "FFT/FWHT ratio", "value": times["cyclic"], "unit": "ms", "n_gpus": 1,
+           "steps": a.steps, "warmup": a.warmup, "higher_is_better": False, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": "planted +-1 correlations n=%d (64 pairs, rho=0.9, B=A^T, FP32 "
+                                  "storage), b=2^%d, d=%d" % (n, L, d)},
+           "ms": times, "fft_over_fwht": round(times["cyclic"] / times["fwht"], 2),
+           "kernels_ms_per_step": kernels, "planted_recall": recall}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -511,6 +555,8 @@ def main():
         return run_precision(a)
     if a.workload == "diff":
         return run_diff(a)
+    if a.workload == "cyclic":
+        return run_cyclic(a)
     return run_cmm(a)
 
 

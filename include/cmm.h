@@ -163,6 +163,40 @@ int cmm_multiply(const void *A, int64_t lda, int32_t transA, const void *B, int6
                  int32_t prec, int32_t reduce, double *C, int64_t ldc, double *R,
                  void *ws, size_t ws_bytes, void *stream);
 
+/* ---- Pagh's original cyclic form (Sec. 3.1), through the FFT --------------
+ * The paper's comparison form: the same sketches x_t, y_t and hash functions,
+ * but the product polynomial is the cyclic convolution of Sec. 2, so
+ *   R_r[w] = sum_{(i,j) : (h1_r(i) + h2_r(j)) mod b = w} s1_r(i) s2_r(j) (A B)[i][j],
+ * computed as R_r = (1/b) IDFT( sum_t DFT(x_t) o DFT(y_t) ).  The forward
+ * transforms and the products run in FP32 (complex, 2^13-frequency slices);
+ * the reduction over t, the inverse transform and the extraction are FP64.
+ * prec must be CMM_PREC_F32 (else CMM_ERR_ARG) and log2b >= 13 (else
+ * CMM_ERR_RANGE); arguments, layouts, ownership and the other errors are those
+ * of cmm_sketch. */
+size_t cmm_sketch_cyclic_workspace_bytes(int64_t m, int64_t k, int64_t p, int32_t d,
+                                         int32_t log2b, int32_t dtype, int32_t prec,
+                                         int32_t transA);
+int cmm_sketch_cyclic(const void *A, int64_t lda, int32_t transA, const void *B, int64_t ldb,
+                      int32_t dtype, int64_t m, int64_t k, int64_t p, const cmm_hashes *hs,
+                      int32_t prec, double *R, void *ws, size_t ws_bytes, void *stream);
+
+/* Decompress of the cyclic form for every entry:
+ *   C[i][j] = reduce_r s1_r(i) s2_r(j) R_r[(h1_r(i) + h2_r(j)) mod b]
+ * (R from cmm_sketch_cyclic; `ws` of cmm_extract_workspace_bytes); otherwise
+ * as cmm_extract.  Heavy hitters of the cyclic estimate: cmm_threshold. */
+int cmm_extract_cyclic(const double *R, const cmm_hashes *hs, int64_t m, int64_t p,
+                       int32_t reduce, double *C, int64_t ldc, void *ws, size_t ws_bytes,
+                       void *stream);
+
+/* cmm_sketch_cyclic then cmm_extract_cyclic (as cmm_multiply). */
+size_t cmm_multiply_cyclic_workspace_bytes(int64_t m, int64_t k, int64_t p, int32_t d,
+                                           int32_t log2b, int32_t dtype, int32_t prec,
+                                           int32_t transA);
+int cmm_multiply_cyclic(const void *A, int64_t lda, int32_t transA, const void *B,
+                        int64_t ldb, int32_t dtype, int64_t m, int64_t k, int64_t p,
+                        const cmm_hashes *hs, int32_t prec, int32_t reduce, double *C,
+                        int64_t ldc, double *R, void *ws, size_t ws_bytes, void *stream);
+
 /* Bytes of `ws` (device) needed by cmm_multiply_host with room for a
  * heavy-hitter list of `capacity` entries. */
 size_t cmm_multiply_host_workspace_bytes(int64_t m, int64_t k, int64_t p, int32_t d,

@@ -76,6 +76,13 @@ def _load() -> ctypes.CDLL:
         "cmm_multiply_host": (ctypes.c_int, [P, i64, i32, P, i64, i32, i64, i64, i64, H, i32, i32,
                                              P, i64, f64, i64, P, P, P,
                                              ctypes.POINTER(ctypes.c_int64), P, sz, P]),
+        "cmm_sketch_cyclic_workspace_bytes": (sz, [i64, i64, i64, i32, i32, i32, i32, i32]),
+        "cmm_sketch_cyclic": (ctypes.c_int, [P, i64, i32, P, i64, i32, i64, i64, i64, H, i32, P,
+                                             P, sz, P]),
+        "cmm_extract_cyclic": (ctypes.c_int, [P, H, i64, i64, i32, P, i64, P, sz, P]),
+        "cmm_multiply_cyclic_workspace_bytes": (sz, [i64, i64, i64, i32, i32, i32, i32, i32]),
+        "cmm_multiply_cyclic": (ctypes.c_int, [P, i64, i32, P, i64, i32, i64, i64, i64, H, i32,
+                                               i32, P, i64, P, P, sz, P]),
         "cmm_mean_pairs": (ctypes.c_int, [P, H, i64, P, P, P, P]),
         "cmm_backward_workspace_bytes": (sz, [i64, i64, i64, i32, i32, i32, i32, i32]),
         "cmm_backward": (ctypes.c_int, [P, i64, i32, P, i64, i32, i64, i64, i64, H, i32, i64,
@@ -271,6 +278,54 @@ def multiply(A: torch.Tensor, B: torch.Tensor, h: Hashes, prec: str = "f32",
                             C.data_ptr(), max(C.stride(0), 1),
                             R.data_ptr() if R is not None else None, ws.data_ptr(),
                             ws.numel(), _stream(stream)))
+    return C
+
+
+def sketch_cyclic(A: torch.Tensor, B: torch.Tensor, h: Hashes, transA: bool = False,
+                  stream=None) -> torch.Tensor:
+    """Compress of Pagh's cyclic form (Sec. 3.1, through the FFT, FP32
+    butterflies): R (d x b, float64, device) with R_r = sum_t x_t * y_t."""
+    m, k, p, dt = _operands(A, B, transA)
+    pr = _PREC["f32"]
+    ws = _workspace(lib.cmm_sketch_cyclic_workspace_bytes(m, k, p, h.d, h.log2b, dt, pr,
+                                                          int(transA)), A.device)
+    R = torch.empty((h.d, h.b), dtype=torch.float64, device=A.device)
+    _check(lib.cmm_sketch_cyclic(A.data_ptr(), max(A.stride(0), 1), int(transA), B.data_ptr(),
+                                 max(B.stride(0), 1), dt, m, k, p, h.ref, pr, R.data_ptr(),
+                                 ws.data_ptr(), ws.numel(), _stream(stream)))
+    return R
+
+
+def extract_cyclic(R: torch.Tensor, h: Hashes, m: int, p: int, reduce: str = "median",
+                   stream=None, out: torch.Tensor | None = None) -> torch.Tensor:
+    """Decompress of the cyclic form: bucket (h1(i) + h2(j)) mod b."""
+    _check_R(R, h)
+    C = out if out is not None else torch.empty((m, p), dtype=torch.float64, device=R.device)
+    ws = _workspace(lib.cmm_extract_workspace_bytes(m, p, h.d), R.device)
+    _check(lib.cmm_extract_cyclic(R.data_ptr(), h.ref, m, p, _REDUCE[reduce], C.data_ptr(),
+                                  max(C.stride(0), 1), ws.data_ptr(), ws.numel(),
+                                  _stream(stream)))
+    return C
+
+
+def multiply_cyclic(A: torch.Tensor, B: torch.Tensor, h: Hashes, reduce: str = "median",
+                    transA: bool = False, R: torch.Tensor | None = None,
+                    out: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+                    stream=None):
+    """sketch_cyclic then extract_cyclic: the m x p float64 estimate of A B."""
+    m, k, p, dt = _operands(A, B, transA)
+    pr = _PREC["f32"]
+    need = lib.cmm_multiply_cyclic_workspace_bytes(m, k, p, h.d, h.log2b, dt, pr, int(transA))
+    if ws is None or ws.numel() < need:
+        ws = _workspace(need, A.device)
+    C = out if out is not None else torch.empty((m, p), dtype=torch.float64, device=A.device)
+    if R is not None:
+        _check_R(R, h)
+    _check(lib.cmm_multiply_cyclic(A.data_ptr(), max(A.stride(0), 1), int(transA),
+                                   B.data_ptr(), max(B.stride(0), 1), dt, m, k, p, h.ref, pr,
+                                   _REDUCE[reduce], C.data_ptr(), max(C.stride(0), 1),
+                                   R.data_ptr() if R is not None else None, ws.data_ptr(),
+                                   ws.numel(), _stream(stream)))
     return C
 
 

@@ -52,6 +52,7 @@ struct SketchPlan {
     bool tmem;             // use the TMEM variant of the FP32 kernel
     // parts along the inner index: part c covers t in [kb[c], kb[c+1]) in
     // pnch[c] blocks of pchunk[c]; nchunks is the total, chunk part 0's
+    int nclass;            // cyclic (FFT) form: frequency classes computed (C/2 + 1)
     int nparts;
     int64_t kb[kMaxParts + 1];
     int64_t pchunk[kMaxParts];
@@ -127,6 +128,18 @@ size_t sketch_bf16_smem();
 cudaError_t launch_sketch_bf16(const SketchPlan &pl, const float *At, const float *Bp, int64_t m,
                                int64_t k, int64_t p, int d, const HashParams &hp, tab_t *tabA,
                                tab_t *tabB, const float *colmax, double *partial, cudaStream_t s);
+// cyclic (FFT) form of Sec. 3.1: 2^13-frequency classes, 32-bit tables of
+// d * nclass * m and d * nclass * p words (built by the launcher), complex FP64
+// partials [block][r][class][2^13][2]; the finish writes G [r][C][2^13][2]
+int sketch_fft_llo();
+int sketch_fft_threads();
+size_t sketch_fft_smem();
+cudaError_t launch_sketch_fft(const SketchPlan &pl, const float *At, const float *Bp, int64_t m,
+                              int64_t k, int64_t p, int d, const HashParams &hp, uint32_t *tabA,
+                              uint32_t *tabB, const float *colmax, double *partial,
+                              cudaStream_t s);
+cudaError_t launch_finish_fft(const double *partial, int nchunks, int d, int L, int C, int NC,
+                              double *G, double *R, cudaStream_t s);
 int sketch_threads_f32(int Llo);
 int sketch_threads_f64(int Llo);
 size_t sketch_smem_f32(int Llo);
@@ -136,10 +149,11 @@ size_t sketch_smem_f64(int Llo);
 cudaError_t launch_hash_tables(const HashParams &hp, int d, int L, int64_t m, int64_t p,
                                uint32_t *H1, uint32_t *H2, cudaStream_t s);
 // rows [0, m) of C; H1 holds each repetition's row hashes at stride ldh (pass
-// H1 + i0 and the full row count to extract rows i0 .. i0 + m - 1)
+// H1 + i0 and the full row count to extract rows i0 .. i0 + m - 1); cyclic
+// selects the bucket (h1 + h2) mod b of Sec. 3.1 instead of h1 XOR h2
 cudaError_t launch_extract(const double *R, const uint32_t *H1, const uint32_t *H2, int d,
                            int L, int64_t m, int64_t p, int reduce, double *C, int64_t ldc,
-                           int64_t ldh, cudaStream_t s);
+                           int64_t ldh, cudaStream_t s, int cyclic = 0);
 cudaError_t launch_hh_count(const double *R, const uint32_t *H1, const uint32_t *H2,
                             const double *C, int64_t ldc, int d, int L, int64_t m, int64_t p,
                             int reduce, double tau, int64_t tile, int64_t ntiles,

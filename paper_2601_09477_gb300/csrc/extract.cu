@@ -44,7 +44,7 @@ __global__ void hash_tables_kernel(const __grid_constant__ HashParams hp, int d,
 
 // dense estimate: a CTA covers kRowsPerBlock rows x kThreads columns; each
 // thread keeps its column's d hash words in registers
-template <int D>
+template <int D, bool CYC>
 __global__ void __launch_bounds__(kThreads) extract_kernel(const double *__restrict__ R,
                                                            const uint32_t *__restrict__ H1,
                                                            const uint32_t *__restrict__ H2, int d,
@@ -69,12 +69,12 @@ __global__ void __launch_bounds__(kThreads) extract_kernel(const double *__restr
 #pragma unroll
         for (int r = 0; r < D; ++r) h2v[r] = H2[(int64_t)r * p + j];
         for (int rr = 0; rr < kRowsPerBlock && i0 + rr < m; ++rr)
-            C[(i0 + rr) * ldc + j] = estimate_fixed<D>(R, b, mask, h1s[rr], h2v, reduce);
+            C[(i0 + rr) * ldc + j] = estimate_fixed<D, CYC>(R, b, mask, h1s[rr], h2v, reduce);
     } else {
         long long v[CMM_MAX_D];
         for (int rr = 0; rr < kRowsPerBlock && i0 + rr < m; ++rr) {
             for (int r = 0; r < d; ++r)
-                v[r] = rep_key(R + r * b, h1s[rr][r], H2[(int64_t)r * p + j], mask);
+                v[r] = rep_key<CYC>(R + r * b, h1s[rr][r], H2[(int64_t)r * p + j], mask);
             C[(i0 + rr) * ldc + j] = combine_generic(v, d, reduce);
         }
     }
@@ -244,19 +244,27 @@ cudaError_t launch_hash_tables(const HashParams &hp, int d, int L, int64_t m, in
 
 #define CMM_ODD_D_CASES(X) X(1) X(3) X(5) X(7) X(9) X(11) X(13) X(15)
 
-cudaError_t launch_extract(const double *R, const uint32_t *H1, const uint32_t *H2, int d, int L,
-                           int64_t m, int64_t p, int reduce, double *C, int64_t ldc, int64_t ldh,
-                           cudaStream_t s) {
+template <bool CYC>
+cudaError_t launch_extract_t(const double *R, const uint32_t *H1, const uint32_t *H2, int d, int L,
+                             int64_t m, int64_t p, int reduce, double *C, int64_t ldc, int64_t ldh,
+                             cudaStream_t s) {
     const int64_t blocks = ((m + kRowsPerBlock - 1) / kRowsPerBlock) * ((p + kThreads - 1) / kThreads);
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     const unsigned g = (unsigned)blocks;
     switch (d) {
-#define X(D) case D: extract_kernel<D><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh); break;
+#define X(D) case D: extract_kernel<D, CYC><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh); break;
         CMM_ODD_D_CASES(X)
 #undef X
-        default: extract_kernel<0><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh);
+        default: extract_kernel<0, CYC><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_extract(const double *R, const uint32_t *H1, const uint32_t *H2, int d, int L,
+                           int64_t m, int64_t p, int reduce, double *C, int64_t ldc, int64_t ldh,
+                           cudaStream_t s, int cyclic) {
+    return cyclic ? launch_extract_t<true>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh, s)
+                  : launch_extract_t<false>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh, s);
 }
 
 cudaError_t launch_hh_count(const double *R, const uint32_t *H1, const uint32_t *H2,

@@ -80,10 +80,13 @@ __device__ inline double combine_generic(long long *v, int d, int reduce) {
     return 0.5 * (val_of_key(v[d / 2 - 1]) + val_of_key(v[d / 2]));
 }
 
-// value of repetition r for packed hash words (bucket | sign << 31)
+// value of repetition r for packed hash words (bucket | sign << 31): bucket
+// h1 XOR h2 (Algorithm 1), or (h1 + h2) mod b for the cyclic form of Sec. 3.1
+// (buckets are below 2^24, so the sum's bit 31 is still the XOR of the signs)
+template <bool CYC = false>
 __device__ __forceinline__ long long rep_key(const double *__restrict__ Rr, uint32_t h1, uint32_t h2,
                                              uint32_t mask) {
-    const uint32_t x = h1 ^ h2;
+    const uint32_t x = CYC ? h1 + h2 : h1 ^ h2;
     const unsigned long long bits =
         (unsigned long long)__double_as_longlong(__ldg(Rr + (x & mask))) ^
         ((unsigned long long)(x >> 31) << 63);
@@ -91,13 +94,13 @@ __device__ __forceinline__ long long rep_key(const double *__restrict__ Rr, uint
 }
 
 // estimate for one (i, j): h1s = the d packed words of row i, h2v = of column j
-template <int D>
+template <int D, bool CYC = false>
 __device__ __forceinline__ double estimate_fixed(const double *__restrict__ R, int64_t b,
                                                  uint32_t mask, const uint32_t *h1s,
                                                  const uint32_t (&h2v)[D], int reduce) {
     long long v[D];
 #pragma unroll
-    for (int r = 0; r < D; ++r) v[r] = rep_key(R + r * b, h1s[r], h2v[r], mask);
+    for (int r = 0; r < D; ++r) v[r] = rep_key<CYC>(R + r * b, h1s[r], h2v[r], mask);
     if (reduce == CMM_MEAN) {
         double s = 0.0;
 #pragma unroll
