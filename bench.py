@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--d", type=int, default=9)
     ap.add_argument("--prec", default="f32", choices=["f32", "f64", "bf16tc"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--no-dgemm", action="store_true", help="skip the cuBLAS DGEMM comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=10)
@@ -320,6 +321,29 @@ def run_cmm(a):
         result["fp64"] = {"ms_per_step": round(f64_ms, 3), "speedup": round(f64_ms / ms, 2),
                           "max_abs_R_diff_vs_fp32": dR,
                           "equal_error": dR == 0.0}
+
+    # cuBLAS DGEMM of the same product on the same GPU (the exact C): time of
+    # one call after one warm-up, and the heavy hitters against the exact C
+    if not a.no_dgemm and world == 1:
+        Cx = torch.matmul(A, B)
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        Cx = torch.matmul(A, B)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        dg_ms = g0.elapsed_time(g1)
+        true_hh = int((Cx.abs() >= tau).sum().item())
+        Ix = torch.from_numpy(Ih.astype(np.int64)).to(dev)
+        Jx = torch.from_numpy(Jh.astype(np.int64)).to(dev)
+        hits = int((Cx[Ix, Jx].abs() >= tau).sum().item()) if len(Ih) else 0
+        result["dgemm"] = {"ms": round(dg_ms, 3), "tflops": round(2.0 * n ** 3 / dg_ms / 1e9, 3),
+                           "speedup_of_sketch_step": round(dg_ms / ms, 2),
+                           "exact_heavy_hitters": true_hh,
+                           "reported_that_are_exact_heavy_hitters": hits,
+                           "exact_heavy_hitters_found": hits / max(true_hh, 1)}
+        del Cx, Ix, Jx
 
     # end to end through the host-buffer C call (pinned host memory)
     if not a.no_e2e:
