@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--workload", default="planted",
-                    choices=["planted", "batched", "precision", "diff", "cyclic"],
+                    choices=["planted", "batched", "precision", "diff", "cyclic", "paper"],
                     help="planted (the headline line) or one of the other configurations")
     ap.add_argument("--tune-budget", type=float, default=120.0)
     return ap.parse_args()
@@ -569,6 +569,66 @@ def run_cyclic(a):
     return 0
 
 
+# the paper's largest instances that fit one GB300 (Minerva, Table 7: FWHT
+# median seconds on 64 cores, FP64): name, n, c_d, c_b, d, log2 b, seconds
+PAPER_ROWS = [
+    ("Logunit", 1 << 15, 0.25, 0.25, 3, 13, 1.0),
+    ("Logunit", 1 << 16, 0.25, 0.25, 5, 14, 7.8),
+    ("Diagonal", 1 << 15, 0.75, 4.00, 11, 17, 11.4),
+    ("Covariance", 1 << 15, 1.50, 4.00, 23, 17, 23.8),
+    ("Lightbulb", 1 << 15, 2.00, 4.00, 31, 17, 32.0),
+    ("Lightbulb", 1 << 16, 2.00, 4.00, 33, 18, 161.1),
+]
+
+
+def run_paper(a):
+    """The paper's instance sizes (n, d, b of its Table 7 rows up to n = 2^16):
+    Compress + Decompress of every entry on one GB300, FP32 butterflies (and the
+    plain FP64 form where it takes a few seconds), next to the paper's FWHT
+    median on 64 CPU cores.  The time depends on (n, d, b) only, so the
+    operands are N(0,1) FP64 matrices of the instance's size (context, not the
+    instances' values)."""
+    import torch
+    from paper_2601_09477_gb300 import cmm
+    torch.cuda.set_device(0)
+    rows = []
+    cur_n, A, B, C = None, None, None, None
+    for name, n, cd, cb, d, L, paper_s in PAPER_ROWS:
+        if n != cur_n:
+            A = B = C = None
+            torch.cuda.empty_cache()
+            g = torch.Generator(device="cuda")
+            g.manual_seed(n)
+            A = torch.randn((n, n), generator=g, dtype=torch.float64, device="cuda")
+            B = torch.randn((n, n), generator=g, dtype=torch.float64, device="cuda")
+            C = torch.empty((n, n), dtype=torch.float64, device="cuda")
+            cur_n = n
+        h = cmm.make_hashes(4000 + d, d, L)
+        row = {"instance": name, "n": n, "c_d": cd, "c_b": cb, "d": d, "log2b": L,
+               "paper_fwht_s_64_cores": paper_s}
+        butterflies = d * n * 2.0 * (1 << L) * L
+        precs = ["f32"] + (["f64"] if butterflies / 0.45e12 < 3.0 else [])
+        for prec in precs:
+            ws = torch.empty(cmm.multiply_workspace_bytes(n, n, n, h, torch.float64, prec),
+                             dtype=torch.uint8, device="cuda")
+            fn = lambda: cmm.multiply(A, B, h, prec=prec, out=C, ws=ws)
+            fn()
+            ms = _events_ms(fn, 1)
+            row[prec + "_s"] = round(ms / 1e3, 4)
+            row[prec + "_speedup_vs_paper"] = round(paper_s / (ms / 1e3), 1)
+            del ws
+        rows.append(row)
+    res = {"metric": "paper-scale instances: Compress + Decompress seconds on one GB300 vs the "
+                     "paper's FWHT median on 64 CPU cores (context)",
+           "value": rows[-1]["f32_s"], "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 1,
+           "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "sizes of the paper's Table 7 rows up to n=2^16, N(0,1) FP64 "
+                                  "operands, d and b from the paper's parameter rule"},
+           "rows": rows}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -581,6 +641,8 @@ def main():
         return run_diff(a)
     if a.workload == "cyclic":
         return run_cyclic(a)
+    if a.workload == "paper":
+        return run_paper(a)
     return run_cmm(a)
 
 
