@@ -1,0 +1,59 @@
+"""The N > 1 path of the benchmark on CPU: world-size-2 gloo process groups.
+
+The path shards into independent replicas (one problem per rank, no data-path
+collective); the only cross-rank steps are the barrier and the maximum of the
+ranks' times, from which the whole-job time per problem follows.  The oracle
+(reference) arm runs on rank 0 only."""
+import os
+import socket
+import sys
+import types
+
+import torch
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import bench
+    torch.distributed.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        got = bench.max_over_ranks(1.5 + rank, world, "cpu")
+        torch.distributed.barrier()
+        # the reference arm: ranks other than 0 leave without work or output
+        ref = bench.run_reference(types.SimpleNamespace()) if rank != 0 else None
+        q.put((rank, got, bench.whole_job_ms(got, world), ref))
+    finally:
+        torch.distributed.destroy_process_group()
+
+
+def test_replicas_max_time_and_whole_job_value_gloo_world2():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [r[:3] for r in res] == [(0, 2.5, 1.25), (1, 2.5, 1.25)]
+    assert res[1][3] == 0
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(3.0, 1, "cpu") == 3.0
+    assert bench.whole_job_ms(3.0, 1) == 3.0
