@@ -83,10 +83,11 @@ __device__ __forceinline__ void reg_fwht(T (&v)[E]) {
     }
 }
 
-// FP32: stage 0 scalar, stages >= 1 on packed pairs (j, j+1) and (j+h, j+h+1)
-template <int E, int NB>
+// FP32: stage 0 scalar, stages >= 1 on packed pairs (j, j+1) and (j+h, j+h+1);
+// SKIP0 leaves out stage 0 (done by the caller)
+template <int E, int NB, bool SKIP0 = false>
 __device__ __forceinline__ void reg_fwht_f32(float (&v)[E]) {
-    if constexpr (NB >= 1) {
+    if constexpr (NB >= 1 && !SKIP0) {
 #pragma unroll
         for (int j = 0; j < E; j += 2) {
             const float a = v[j], b = v[j + 1];

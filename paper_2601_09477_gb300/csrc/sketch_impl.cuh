@@ -23,7 +23,7 @@
 // FP32 butterflies take the scatter in fixed point: shared-memory FP32 atomic
 // adds are far slower than integer ones, so each column is scattered as the
 // 32-bit integers round(a * 2^e), with one power of two per (CTA, column)
-// such that c_max * max_i |a_i| * 2^e < 2^30 (c_max: the most elements that
+// such that c_max * max_i |a_i| * 2^e < 2^29 (c_max: the most elements that
 // share a bucket of the CTA's slice, counted once per CTA).  The bucket sums
 // are exact, independent of the order of the atomics and below 2^31; round 0
 // of the transform converts them to FP32 and scales back by 2^-e.  The column
@@ -124,14 +124,15 @@ __device__ __forceinline__ void scatter_table(T *Sg, const T *__restrict__ col,
 
 // ---- fixed-point scatter (FP32 butterflies) ----
 
-// the power of two 2^e of one column: cmax * colmax * 2^e < 2^30, with e kept
+// the power of two 2^e of one column: cmax * colmax * 2^e < 2^29 (a bucket sum
+// stays below 2^29 + cmax, so sums and differences of two fit 32 bits), with e kept
 // in [-126, 126] so that 2^e and 2^-e are normal floats
 __device__ __forceinline__ void fixed_scale(float colmax, int cmax, float &s, float &inv) {
     // colmax < 2^Ec (exponent field - 126; 0 and subnormals give -126) and
     // cmax < 2^Ek, so the product is below 2^(Ec + Ek)
     const int Ec = ((__float_as_int(colmax) >> 23) & 0xff) - 126;
     const int Ek = 32 - __clz(cmax);
-    const int e = min(max(30 - Ec - Ek, -126), 126);
+    const int e = min(max(29 - Ec - Ek, -126), 126);
     s = __int_as_float((127 + e) << 23);
     inv = __int_as_float((127 - e) << 23);
 }

@@ -17,13 +17,13 @@
 // Scatter in fixed point.  Shared-memory FP32 atomic adds are far slower than
 // integer ones on this GPU, so each column is scattered as 32-bit integers:
 // value a becomes round(a * 2^e), with one power of two 2^e per (CTA, column)
-// chosen so that c_max * max_i |a_i| * 2^e < 2^30, c_max being the largest
+// chosen so that c_max * max_i |a_i| * 2^e < 2^29, c_max being the largest
 // number of elements that share a bucket in this CTA's table.  Every bucket
 // sum is then an exact integer below 2^31 (no overflow, no dependence on the
 // order of the atomics), and it is rounded once to FP32 and scaled back by
 // 2^-e when the first register round reads it.  The only error beyond FP32's
 // is the quantisation of each value to a multiple of 2^-e, at most
-// c_max * max|a| * 2^-30; integer-valued inputs (+-1) stay exact.
+// c_max * max|a| * 2^-28; integer-valued inputs (+-1) stay exact.
 //
 // Layout of the slice in shared memory: element u at word u + 4 * (u >> 7).
 // Round 0: thread q holds u = 128 q + j (a contiguous, 16-byte aligned row of
@@ -131,6 +131,9 @@ __device__ __forceinline__ void tmem_st16(uint32_t addr, const float *x) {
 // the 2^14-point FWHT of the slice S in two register rounds; result in v
 // with v[j] = element q + 128 j; the slice is left zeroed.  On entry S holds
 // the integer bucket sums of the fixed-point scatter, scaled back by inv.
+// The first butterfly stage runs on those integers (|sum| < 2^29 + c_max, so
+// a + b and a - b are exact 32-bit integers), off the FP32 pipe, and each
+// result is rounded once.
 __device__ __forceinline__ void tm_fwht(float *S, float (&v)[kTmE], int q, float inv) {
     float4 *row = reinterpret_cast<float4 *>(S + 132 * q);
     const int4 *irow = reinterpret_cast<const int4 *>(row);
@@ -138,23 +141,25 @@ __device__ __forceinline__ void tm_fwht(float *S, float (&v)[kTmE], int q, float
 #pragma unroll
     for (int c = 0; c < kTmE / 4; ++c) {
         const int4 w = irow[c];
-        const float2 lo = __fmul2_rn(make_float2(__int2float_rn(w.x), __int2float_rn(w.y)), inv2);
-        const float2 hi = __fmul2_rn(make_float2(__int2float_rn(w.z), __int2float_rn(w.w)), inv2);
+        const float2 lo = __fmul2_rn(make_float2(__int2float_rn(w.x + w.y), __int2float_rn(w.x - w.y)), inv2);
+        const float2 hi = __fmul2_rn(make_float2(__int2float_rn(w.z + w.w), __int2float_rn(w.z - w.w)), inv2);
         v[4 * c] = lo.x;
         v[4 * c + 1] = lo.y;
         v[4 * c + 2] = hi.x;
         v[4 * c + 3] = hi.y;
     }
-    reg_fwht_f32<kTmE, kTmLE>(v);
+    reg_fwht_f32<kTmE, kTmLE, true>(v);
 #pragma unroll
     for (int c = 0; c < kTmE / 4; ++c)
         row[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < kTmE; ++j) v[j] = S[q + 132 * j];
-    reg_fwht_f32<kTmE, kTmLE>(v);
+    // every column has been read: clear this thread's row for the next scatter
+    __syncthreads();
 #pragma unroll
-    for (int j = 0; j < kTmE; ++j) S[q + 132 * j] = 0.f;
+    for (int c = 0; c < kTmE / 4; ++c) row[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    reg_fwht_f32<kTmE, kTmLE>(v);
 }
 
 // largest number of table entries that share a bucket (the slice Si must be
