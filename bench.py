@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--workload", default="planted",
-                    choices=["planted", "batched", "precision", "diff", "cyclic", "paper"],
+                    choices=["planted", "batched", "precision", "diff", "cyclic", "paper",
+                             "instances"],
                     help="planted (the headline line) or one of the other configurations")
     ap.add_argument("--tune-budget", type=float, default=120.0)
     return ap.parse_args()
@@ -584,6 +585,46 @@ def run_cyclic(a):
     return 0
 
 
+def run_instances(a):
+    """The paper's four instance families (Sec. 5.2) at n = 4096 with the
+    parameters of Table 3: multiply ms (FP32 and FP64 butterflies) and the
+    counters and category of Sec. 5.3 / 5.6 for each."""
+    import torch
+    from paper_2601_09477_gb300 import cmm
+    from paper_2601_09477_gb300 import evaluate as ev
+    torch.cuda.set_device(0)
+    n = 4096
+    rows = []
+    for name, cd, cb in [("logunit", 1.0, 0.5), ("logunit", 0.25, 1.0), ("diagonal", 2.0, 4.0),
+                         ("diagonal", 0.75, 4.0), ("covariance", 1.5, 4.0),
+                         ("lightbulb", 2.0, 4.0)]:
+        d, L = ev.params(n, cd, cb)
+        A, B, Ct, big = ev.instance(name, n, seed=1)
+        h = cmm.make_hashes(7, d, L)
+        row = {"instance": name, "c_d": cd, "c_b": cb, "d": d, "log2b": L}
+        for prec in ("f32", "f64"):
+            ws = torch.empty(cmm.multiply_workspace_bytes(n, n, n, h, torch.float64, prec),
+                             dtype=torch.uint8, device="cuda")
+            C = torch.empty((n, n), dtype=torch.float64, device="cuda")
+            fn = lambda: cmm.multiply(A, B, h, prec=prec, out=C, ws=ws)
+            for _ in range(a.warmup):
+                fn()
+            row[prec + "_ms"] = round(_events_ms(fn, a.steps), 3)
+            cnt = ev.counters(C, big, Ct)
+            row[prec + "_category"] = ev.category(cnt, n)
+            if prec == "f32":
+                row["counters"] = cnt
+        rows.append(row)
+    res = {"metric": "paper instances at n=4096 (Table 3 parameters): multiply ms and the "
+                     "category reached (Sec. 5.3 counters)", "value": rows[0]["f32_ms"],
+           "unit": "ms", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+           "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "Logunit, Diagonal, Covariance, Lightbulb generators, n=4096, "
+                                  "FP64 storage"}, "rows": rows}
+    print(json.dumps(res), flush=True)
+    return 0
+
+
 # the paper's largest instances that fit one GB300 (Minerva, Table 7: FWHT
 # median seconds on 64 cores, FP64): name, n, c_d, c_b, d, log2 b, seconds
 PAPER_ROWS = [
@@ -658,6 +699,8 @@ def main():
         return run_cyclic(a)
     if a.workload == "paper":
         return run_paper(a)
+    if a.workload == "instances":
+        return run_instances(a)
     return run_cmm(a)
 
 

@@ -242,7 +242,8 @@ cudaError_t launch_hash_tables(const HashParams &hp, int d, int L, int64_t m, in
     return cudaGetLastError();
 }
 
-#define CMM_ODD_D_CASES(X) X(1) X(3) X(5) X(7) X(9) X(11) X(13) X(15)
+#define CMM_ODD_D_CASES(X) X(1) X(3) X(5) X(7) X(9) X(11) X(13) X(15) X(17) X(19) X(21) X(23) \
+    X(25) X(27) X(29) X(31) X(33)
 
 template <bool CYC>
 cudaError_t launch_extract_t(const double *R, const uint32_t *H1, const uint32_t *H2, int d, int L,

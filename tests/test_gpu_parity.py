@@ -210,7 +210,7 @@ def test_sketch_empty_inner_dimension(cmm):
     assert torch.count_nonzero(R).item() == 0
 
 
-@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 7, 9, 11, 16, 17])
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 7, 9, 11, 16, 17, 25, 33, 35])
 @pytest.mark.parametrize("reduce", ["median", "mean"])
 def test_extract_bitwise_given_R(cmm, d, reduce):
     m, p, L = 67, 301, 9
@@ -223,7 +223,7 @@ def test_extract_bitwise_given_R(cmm, d, reduce):
     assert np.array_equal(C, Co)
 
 
-@pytest.mark.parametrize("d", [3, 4, 9])
+@pytest.mark.parametrize("d", [3, 4, 9, 21])
 def test_heavy_hitters_given_R(cmm, d):
     m, p, L = 150, 230, 8
     g = np.random.default_rng(100 + d)
