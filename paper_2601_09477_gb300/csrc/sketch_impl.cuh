@@ -32,10 +32,10 @@
 //
 // The scatter either evaluates the hashes per element (multiply-add-shift,
 // two 64-bit products) or, in the single-problem kernel, reads one packed
-// 32-bit word per element from a table built once per call for the CTA's
-// (r, u_hi): the padded shared-memory word of the bucket in the low bits and
-// the combined sign in bit 31.  The table is re-read for every t and stays in
-// L1; the operand columns are streamed past L1.
+// 16-bit word per element from a table built once per call for the CTA's
+// (r, u_hi): the padded shared-memory word of the bucket in bits 0-14 and the
+// combined sign in bit 15.  The table is re-read for every t and stays in L1;
+// the operand columns are streamed past L1.
 #pragma once
 
 #include "cmm_internal.h"
@@ -89,7 +89,7 @@ __device__ __forceinline__ void scatter_column(T *Sg, const T *__restrict__ col,
     }
 }
 
-// scatter one column using the packed (padded word | sign << 31) table
+// scatter one column using the packed (padded word | sign << 15) table
 template <typename T, int L, int LE, int B = 8>
 __device__ __forceinline__ void scatter_table(T *Sg, const T *__restrict__ col,
                                               const tab_t *__restrict__ tab, int64_t n, int q) {
@@ -398,7 +398,7 @@ sketch_kernel(const T *__restrict__ At, int64_t ldat, const T *__restrict__ Bp, 
 }
 
 // packed scatter words for every (r, u_hi) slot: tab[(r*C + u_hi)*n + x] =
-// padded shared-memory word of h_lo(x) | (combined sign bit) << 31
+// padded shared-memory word of h_lo(x) | (combined sign bit) << 15
 template <typename T, int L, int LE>
 __global__ void sketch_table_kernel(const __grid_constant__ HashParams hp, int d, int Lfull,
                                     int Llo, int C, int64_t m, int64_t p,
