@@ -237,10 +237,15 @@ def run_cmm(a):
     R = torch.empty((d, 1 << L), dtype=torch.float64, device=dev)
     C = torch.empty((n, n), dtype=torch.float64, device=dev)
     cap = 1 << 22
+    hh = (torch.empty(cap, dtype=torch.int32, device=dev),
+          torch.empty(cap, dtype=torch.int32, device=dev),
+          torch.empty(cap, dtype=torch.float64, device=dev))
 
     def step(prec):
-        cmm.multiply(A, B, h, prec=prec, R=R, out=C, ws=ws)
-        return cmm.threshold(C, tau, capacity=cap)
+        # Compress, Decompress and the ordered heavy-hitter list in one call
+        _, lst = cmm.multiply_threshold(A, B, h, tau, capacity=cap, prec=prec, R=R, out=C, ws=ws,
+                                        hh=hh)
+        return lst
 
     def barrier():
         if world > 1:

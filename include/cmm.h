@@ -163,6 +163,21 @@ int cmm_multiply(const void *A, int64_t lda, int32_t transA, const void *B, int6
                  int32_t prec, int32_t reduce, double *C, int64_t ldc, double *R,
                  void *ws, size_t ws_bytes, void *stream);
 
+/* cmm_multiply followed by cmm_threshold(C, tau) in one call, with the
+ * per-row heavy-hitter counts taken while Decompress writes C (Algorithm 1's
+ * Decompress, then the goal of Sec. 1), so the list costs one ordered pass
+ * over C instead of two.  Outputs as cmm_multiply (C, R) plus the list of
+ * cmm_threshold: I, J (device int32), V (device FP64), `capacity` entries,
+ * *count (HOST) = total found.  Synchronises `stream` to read the count.
+ * `ws`: cmm_multiply_workspace_bytes.  Errors: as cmm_multiply, plus
+ * CMM_ERR_CAPACITY as in cmm_threshold. */
+int cmm_multiply_threshold(const void *A, int64_t lda, int32_t transA, const void *B,
+                           int64_t ldb, int32_t dtype, int64_t m, int64_t k, int64_t p,
+                           const cmm_hashes *hs, int32_t prec, int32_t reduce, double *C,
+                           int64_t ldc, double *R, double tau, int32_t *I, int32_t *J,
+                           double *V, int64_t capacity, int64_t *count, void *ws,
+                           size_t ws_bytes, void *stream);
+
 /* ---- Pagh's original cyclic form (Sec. 3.1), through the FFT --------------
  * The paper's comparison form: the same sketches x_t, y_t and hash functions,
  * but the product polynomial is the cyclic convolution of Sec. 2, so

@@ -72,6 +72,9 @@ def _load() -> ctypes.CDLL:
         "cmm_multiply_workspace_bytes": (sz, [i64, i64, i64, i32, i32, i32, i32, i32]),
         "cmm_multiply": (ctypes.c_int, [P, i64, i32, P, i64, i32, i64, i64, i64, H, i32, i32,
                                         P, i64, P, P, sz, P]),
+        "cmm_multiply_threshold": (ctypes.c_int, [P, i64, i32, P, i64, i32, i64, i64, i64, H,
+                                                  i32, i32, P, i64, P, f64, P, P, P, i64,
+                                                  ctypes.POINTER(ctypes.c_int64), P, sz, P]),
         "cmm_multiply_host_workspace_bytes": (sz, [i64, i64, i64, i32, i32, i32, i32, i32, i64]),
         "cmm_multiply_host": (ctypes.c_int, [P, i64, i32, P, i64, i32, i64, i64, i64, H, i32, i32,
                                              P, i64, f64, i64, P, P, P,
@@ -279,6 +282,42 @@ def multiply(A: torch.Tensor, B: torch.Tensor, h: Hashes, prec: str = "f32",
                             R.data_ptr() if R is not None else None, ws.data_ptr(),
                             ws.numel(), _stream(stream)))
     return C
+
+
+def multiply_threshold(A: torch.Tensor, B: torch.Tensor, h: Hashes, tau: float,
+                       capacity: int = 1 << 20, prec: str = "f32", reduce: str = "median",
+                       transA: bool = False, R: torch.Tensor | None = None,
+                       out: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+                       hh=None, stream=None):
+    """cmm_multiply and cmm_threshold in one call: the m x p float64 estimate
+    and (I, J, V) of every |estimate| >= tau in (i, j) order.  ``hh`` may hold
+    preallocated (I, J, V) device buffers of at least ``capacity`` entries."""
+    m, k, p, dt = _operands(A, B, transA)
+    pr = _PREC[prec]
+    dev = A.device
+    need = lib.cmm_multiply_workspace_bytes(m, k, p, h.d, h.log2b, dt, pr, int(transA))
+    if ws is None or ws.numel() < need:
+        ws = _workspace(need, dev)
+    C = out if out is not None else torch.empty((m, p), dtype=torch.float64, device=dev)
+    if R is not None:
+        _check_R(R, h)
+    if hh is None:
+        hh = (torch.empty(max(capacity, 1), dtype=torch.int32, device=dev),
+              torch.empty(max(capacity, 1), dtype=torch.int32, device=dev),
+              torch.empty(max(capacity, 1), dtype=torch.float64, device=dev))
+    I, J, V = hh
+    if min(I.numel(), J.numel(), V.numel()) < capacity:
+        raise ValueError("heavy-hitter buffers hold fewer than capacity entries")
+    cnt = ctypes.c_int64(0)
+    _check(lib.cmm_multiply_threshold(A.data_ptr(), max(A.stride(0), 1), int(transA),
+                                      B.data_ptr(), max(B.stride(0), 1), dt, m, k, p, h.ref, pr,
+                                      _REDUCE[reduce], C.data_ptr(), max(C.stride(0), 1),
+                                      R.data_ptr() if R is not None else None, float(tau),
+                                      I.data_ptr(), J.data_ptr(), V.data_ptr(), capacity,
+                                      ctypes.byref(cnt), ws.data_ptr(), ws.numel(),
+                                      _stream(stream)))
+    n = cnt.value
+    return C, (I[:n], J[:n], V[:n])
 
 
 def sketch_cyclic(A: torch.Tensor, B: torch.Tensor, h: Hashes, transA: bool = False,

@@ -22,6 +22,17 @@ struct HashParams {
     HashRep rep[CMM_MAX_D];
 };
 
+// The heavy-hitter test abs(e) >= tau as an integer range on the magnitude
+// bits of e (sign bit cleared): lo <= |bits(e)| <= hi.  tau <= 0 (either
+// zero) gives [0, bits(+inf)], tau > 0 gives [bits(tau), bits(+inf)], and a
+// NaN tau the empty range [1, 0]; NaN estimates lie above bits(+inf) and never
+// pass, exactly as the FP64 comparison decides.  Integer compares keep the
+// test off the FP64 pipe.
+struct HhRange {
+    unsigned long long lo, hi;
+};
+HhRange hh_range(double tau);
+
 // One scatter-table word: padded shared-memory index of the bucket in the low
 // 15 bits (slices of at most 2^14 points plus padding), the sign in bit 15.
 using tab_t = uint16_t;
@@ -87,10 +98,15 @@ cudaError_t launch_convert_out(const void *src, int src_f64, int64_t rows, int64
 int set_error(int code, const char *msg);
 
 // ---- launchers (sketch.cu / sketch_f64.cu / finish.cu) ----
+// A^T (k x m) and B (k x p) in the butterfly type.  With FP32 output and rmax
+// non-null, also rmax[t] = max(rmax[t], max |row t of the output|) (rmax
+// zeroed by the caller): the row maxima of launch_rowmax without a second read.
 cudaError_t launch_prep_A(const void *A, int64_t lda, int transA, int dtype, int prec,
-                          int64_t m, int64_t k, void *At, int64_t ldat, cudaStream_t s);
+                          int64_t m, int64_t k, void *At, int64_t ldat, cudaStream_t s,
+                          float *rmax = nullptr);
 cudaError_t launch_prep_B(const void *B, int64_t ldb, int dtype, int prec,
-                          int64_t k, int64_t p, void *Bp, int64_t ldbp, cudaStream_t s);
+                          int64_t k, int64_t p, void *Bp, int64_t ldbp, cudaStream_t s,
+                          float *rmax = nullptr);
 // out[r] = max_c |X[r][c]| over the rows x cols FP32 array X (leading dimension
 // ldx): the per-column scale of the fixed-point scatter
 cudaError_t launch_rowmax(const float *X, int64_t ldx, int64_t rows, int64_t cols, float *out,
@@ -151,19 +167,37 @@ cudaError_t launch_hash_tables(const HashParams &hp, int d, int L, int64_t m, in
 // rows [0, m) of C; H1 holds each repetition's row hashes at stride ldh (pass
 // H1 + i0 and the full row count to extract rows i0 .. i0 + m - 1); cyclic
 // selects the bucket (h1 + h2) mod b of Sec. 3.1 instead of h1 XOR h2
+// With tcounts non-null the kernel also writes, per row i and tile of
+// hh_tiles columns, the number of its estimates inside the heavy-hitter range
+// hr to tcounts[i * ldt + tile], so that the list can be written without a
+// counting pass over C.
 cudaError_t launch_extract(const double *R, const uint32_t *H1, const uint32_t *H2, int d,
                            int L, int64_t m, int64_t p, int reduce, double *C, int64_t ldc,
-                           int64_t ldh, cudaStream_t s, int cyclic = 0);
-cudaError_t launch_hh_count(const double *R, const uint32_t *H1, const uint32_t *H2,
-                            const double *C, int64_t ldc, int d, int L, int64_t m, int64_t p,
-                            int reduce, double tau, int64_t tile, int64_t ntiles,
+                           int64_t ldh, cudaStream_t s, int cyclic = 0, HhRange hr = {1, 0},
+                           int32_t *tcounts = nullptr, int64_t ldt = 0);
+// heavy hitters from R (estimates recomputed; C not written): hits per row,
+// then the ordered list
+cudaError_t launch_hh_count(const double *R, const uint32_t *H1, const uint32_t *H2, int d,
+                            int L, int64_t m, int64_t p, int reduce, HhRange hr,
                             int64_t *counts, cudaStream_t s);
 cudaError_t launch_hh_scan(int64_t *counts, int64_t ntiles, cudaStream_t s);
-cudaError_t launch_hh_write(const double *R, const uint32_t *H1, const uint32_t *H2,
-                            const double *C, int64_t ldc, int d, int L, int64_t m, int64_t p,
-                            int reduce, double tau, int64_t tile, int64_t ntiles,
+cudaError_t launch_hh_write(const double *R, const uint32_t *H1, const uint32_t *H2, int d,
+                            int L, int64_t m, int64_t p, int reduce, HhRange hr,
                             const int64_t *offsets, int32_t *I, int32_t *J, double *V,
                             int64_t capacity, cudaStream_t s);
+// heavy hitters of a dense m x p estimate C: hits per (row, tile) (the same
+// tiles as launch_extract's counts); per row, the tile counts turned in place
+// into their inclusive prefix and the row total into counts[i]; then the
+// ordered list, one warp per tile that holds hits
+int64_t hh_tiles(int64_t p);
+cudaError_t launch_hh_tile_count(const double *C, int64_t ldc, int64_t m, int64_t p, HhRange hr,
+                                 int32_t *tcounts, int64_t ldt, cudaStream_t s);
+cudaError_t launch_hh_rowscan(int32_t *tcounts, int64_t ldt, int64_t m, int64_t p,
+                              int64_t *counts, cudaStream_t s);
+cudaError_t launch_hh_tile_write(const double *C, int64_t ldc, int64_t m, int64_t p, HhRange hr,
+                                 const int32_t *tinc, int64_t ldt, const int64_t *offsets,
+                                 int32_t *I, int32_t *J, double *V, int64_t capacity,
+                                 cudaStream_t s);
 cudaError_t launch_mean_pairs(const double *R, const HashParams &hp, int d, int L, int64_t P,
                               const int32_t *I, const int32_t *J, double *out, cudaStream_t s);
 

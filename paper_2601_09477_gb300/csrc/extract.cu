@@ -7,6 +7,8 @@
 // instructions (the FP64 pipe of this GPU is ~1/70 of the FP32 rate): a sign
 // is an XOR of bit 63, and the median network compares the order-preserving
 // integer key of each double (magnitude bits flipped for negatives).
+#include <cstring>
+
 #include "cmm_internal.h"
 #include "extract_device.cuh"
 
@@ -16,6 +18,18 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kRowsPerBlock = 16;
+// The heavy-hitter passes over a dense estimate count hits per (row, tile of
+// kHhTile columns); the tile is the extraction kernel's column tile, so the
+// counts come for free while Decompress writes C.
+constexpr int kHhTile = kThreads;
+static_assert(kHhTile == 256, "a warp reads a tile as 8 coalesced loads per lane");
+
+// abs(e) >= tau, decided on the magnitude bits (see HhRange)
+__device__ __forceinline__ bool hh_hit(double e, HhRange hr) {
+    const unsigned long long mag =
+        (unsigned long long)__double_as_longlong(e) & 0x7fffffffffffffffull;
+    return mag >= hr.lo && mag <= hr.hi;
+}
 
 __global__ void hash_tables_kernel(const __grid_constant__ HashParams hp, int d, int L, int64_t m,
                                    int64_t p, uint32_t *__restrict__ H1, uint32_t *__restrict__ H2) {
@@ -43,39 +57,71 @@ __global__ void hash_tables_kernel(const __grid_constant__ HashParams hp, int d,
 }
 
 // dense estimate: a CTA covers kRowsPerBlock rows x kThreads columns; each
-// thread keeps its column's d hash words in registers
-template <int D, bool CYC>
+// thread keeps its column's d hash words in registers.  With CNT the CTA also
+// writes, for each of its rows, the number of its estimates that pass the
+// heavy-hitter test: tcounts[i * ldt + column tile] (one bit per row and
+// thread during the row loop, counted after it).
+template <int D, bool CYC, bool CNT>
 __global__ void __launch_bounds__(kThreads) extract_kernel(const double *__restrict__ R,
                                                            const uint32_t *__restrict__ H1,
                                                            const uint32_t *__restrict__ H2, int d,
                                                            int L, int64_t m, int64_t p, int reduce,
                                                            double *__restrict__ C, int64_t ldc,
-                                                           int64_t ldh) {
+                                                           int64_t ldh, HhRange hr,
+                                                           int32_t *__restrict__ tcounts,
+                                                           int64_t ldt) {
     __shared__ uint32_t h1s[kRowsPerBlock][CMM_MAX_D];
+    __shared__ int s_cnt[kRowsPerBlock][kThreads / 32];
     const int64_t b = (int64_t)1 << L;
     const uint32_t mask = (uint32_t)(b - 1);
     const int64_t col_tiles = (p + kThreads - 1) / kThreads;
+    const int64_t tile = blockIdx.x % col_tiles;
     const int64_t i0 = (blockIdx.x / col_tiles) * kRowsPerBlock;
-    const int64_t j = (blockIdx.x % col_tiles) * kThreads + threadIdx.x;
+    const int64_t j = tile * kThreads + threadIdx.x;
     const int dd = D > 0 ? D : d;
     for (int e = threadIdx.x; e < kRowsPerBlock * dd; e += kThreads) {
         const int rr = e / dd, r = e % dd;
         h1s[rr][r] = (i0 + rr < m) ? H1[(int64_t)r * ldh + i0 + rr] : 0u;
     }
     __syncthreads();
-    if (j >= p) return;
-    if constexpr (D > 0) {
-        uint32_t h2v[D];
+    uint32_t hits = 0;   // bit rr: row i0 + rr passes the heavy-hitter test here
+    if (j < p) {
+        if constexpr (D > 0) {
+            uint32_t h2v[D];
 #pragma unroll
-        for (int r = 0; r < D; ++r) h2v[r] = H2[(int64_t)r * p + j];
-        for (int rr = 0; rr < kRowsPerBlock && i0 + rr < m; ++rr)
-            C[(i0 + rr) * ldc + j] = estimate_fixed<D, CYC>(R, b, mask, h1s[rr], h2v, reduce);
-    } else {
-        long long v[CMM_MAX_D];
-        for (int rr = 0; rr < kRowsPerBlock && i0 + rr < m; ++rr) {
-            for (int r = 0; r < d; ++r)
-                v[r] = rep_key<CYC>(R + r * b, h1s[rr][r], H2[(int64_t)r * p + j], mask);
-            C[(i0 + rr) * ldc + j] = combine_generic(v, d, reduce);
+            for (int r = 0; r < D; ++r) h2v[r] = H2[(int64_t)r * p + j];
+#pragma unroll 1
+            for (int rr = 0; rr < kRowsPerBlock && i0 + rr < m; ++rr) {
+                const double e = estimate_fixed<D, CYC>(R, b, mask, h1s[rr], h2v, reduce);
+                C[(i0 + rr) * ldc + j] = e;
+                if constexpr (CNT) hits |= (uint32_t)hh_hit(e, hr) << rr;
+            }
+        } else {
+            long long v[CMM_MAX_D];
+            for (int rr = 0; rr < kRowsPerBlock && i0 + rr < m; ++rr) {
+                for (int r = 0; r < d; ++r)
+                    v[r] = rep_key<CYC>(R + r * b, h1s[rr][r], H2[(int64_t)r * p + j], mask);
+                const double e = combine_generic(v, d, reduce);
+                C[(i0 + rr) * ldc + j] = e;
+                if constexpr (CNT) hits |= (uint32_t)hh_hit(e, hr) << rr;
+            }
+        }
+    }
+    if constexpr (CNT) {
+        // lanes past p (and rows past m) hold no bits
+        const int warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int rr = 0; rr < kRowsPerBlock; ++rr) {
+            const unsigned bal = __ballot_sync(0xffffffffu, (hits >> rr) & 1u);
+            if ((threadIdx.x & 31) == 0) s_cnt[rr][warp] = __popc(bal);
+        }
+        __syncthreads();
+        const int rr = threadIdx.x;
+        if (rr < kRowsPerBlock && i0 + rr < m) {
+            int c = 0;
+#pragma unroll
+            for (int w = 0; w < kThreads / 32; ++w) c += s_cnt[rr][w];
+            tcounts[(i0 + rr) * ldt + tile] = c;
         }
     }
 }
@@ -97,26 +143,21 @@ __device__ __forceinline__ double estimate_at(const double *__restrict__ R, int6
     }
 }
 
-// heavy hitters, pass 1: hits per row (from R when C is null, else from C)
+// heavy hitters from R, pass 1: hits per row
 template <int D>
 __global__ void __launch_bounds__(kThreads) hh_count_kernel(
     const double *__restrict__ R, const uint32_t *__restrict__ H1, const uint32_t *__restrict__ H2,
-    const double *__restrict__ C, int64_t ldc, int d, int L, int64_t m, int64_t p, int reduce,
-    double tau, int64_t *__restrict__ counts) {
+    int d, int L, int64_t m, int64_t p, int reduce, HhRange hr, int64_t *__restrict__ counts) {
     __shared__ uint32_t h1s[CMM_MAX_D];
     __shared__ int64_t wsum[kThreads / 32];
     const int64_t b = (int64_t)1 << L;
     const uint32_t mask = (uint32_t)(b - 1);
     for (int64_t i = blockIdx.x; i < m; i += gridDim.x) {
-        if (!C) {
-            for (int r = threadIdx.x; r < d; r += kThreads) h1s[r] = H1[(int64_t)r * m + i];
-            __syncthreads();
-        }
+        for (int r = threadIdx.x; r < d; r += kThreads) h1s[r] = H1[(int64_t)r * m + i];
+        __syncthreads();
         int64_t cnt = 0;
-        for (int64_t j = threadIdx.x; j < p; j += kThreads) {
-            const double e = C ? C[i * ldc + j] : estimate_at<D>(R, b, mask, h1s, H2, p, j, d, reduce);
-            cnt += fabs(e) >= tau;
-        }
+        for (int64_t j = threadIdx.x; j < p; j += kThreads)
+            cnt += hh_hit(estimate_at<D>(R, b, mask, h1s, H2, p, j, d, reduce), hr);
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
         __syncthreads();
@@ -129,39 +170,51 @@ __global__ void __launch_bounds__(kThreads) hh_count_kernel(
     }
 }
 
-// exclusive scan of counts[0..n) into offsets[0..n] (offsets[n] = total); one CTA
+// exclusive scan of counts[0..n) into offsets[0..n] (offsets[n] = total); one
+// CTA of 1024 threads, thread q owning the contiguous chunk q of the input:
+// chunk sums, one block-wide scan of the 1024 sums, then each chunk's prefixes
 __global__ void __launch_bounds__(1024) hh_scan_kernel(const int64_t *__restrict__ counts,
                                                        int64_t n, int64_t *__restrict__ offsets) {
-    __shared__ int64_t part[1024];
-    __shared__ int64_t carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int64_t base = 0; base < n; base += 1024) {
-        const int64_t idx = base + threadIdx.x;
-        const int64_t v = idx < n ? counts[idx] : 0;
-        part[threadIdx.x] = v;
-        __syncthreads();
-        for (int o = 1; o < 1024; o <<= 1) {
-            const int64_t add = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
-            __syncthreads();
-            part[threadIdx.x] += add;
-            __syncthreads();
-        }
-        if (idx < n) offsets[idx] = carry + part[threadIdx.x] - v;
-        __syncthreads();
-        if (threadIdx.x == 1023) carry += part[1023];
-        __syncthreads();
+    __shared__ int64_t wsum[32];
+    const int q = threadIdx.x, lane = q & 31, warp = q >> 5;
+    const int64_t chunk = (n + 1023) / 1024;
+    const int64_t b0 = q * chunk < n ? q * chunk : n;
+    const int64_t b1 = b0 + chunk < n ? b0 + chunk : n;
+    int64_t s = 0;
+    for (int64_t i = b0; i < b1; ++i) s += counts[i];
+    int64_t inc = s;   // inclusive scan within the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
     }
-    if (threadIdx.x == 0) offsets[n] = carry;
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = wsum[lane], wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t v = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += v;
+        }
+        wsum[lane] = wi - w;   // exclusive prefix of the warp totals
+    }
+    __syncthreads();
+    int64_t run = wsum[warp] + inc - s;
+    for (int64_t i = b0; i < b1; ++i) {
+        offsets[i] = run;
+        run += counts[i];
+    }
+    if (q == 1023) offsets[n] = run;
 }
 
-// heavy hitters, pass 2: ordered compaction of each row's hits
+// heavy hitters from R, pass 2: ordered compaction of each row's hits
 template <int D>
 __global__ void __launch_bounds__(kThreads) hh_write_kernel(
     const double *__restrict__ R, const uint32_t *__restrict__ H1, const uint32_t *__restrict__ H2,
-    const double *__restrict__ C, int64_t ldc, int d, int L, int64_t m, int64_t p, int reduce,
-    double tau, const int64_t *__restrict__ offsets, int32_t *__restrict__ I,
-    int32_t *__restrict__ J, double *__restrict__ V, int64_t capacity) {
+    int d, int L, int64_t m, int64_t p, int reduce, HhRange hr,
+    const int64_t *__restrict__ offsets, int32_t *__restrict__ I, int32_t *__restrict__ J,
+    double *__restrict__ V, int64_t capacity) {
     __shared__ uint32_t h1s[CMM_MAX_D];
     __shared__ int wcount[kThreads / 32];
     const int64_t b = (int64_t)1 << L;
@@ -171,17 +224,15 @@ __global__ void __launch_bounds__(kThreads) hh_write_kernel(
         int64_t off = offsets[i];
         const int64_t end = offsets[i + 1];
         if (off == end || off >= capacity) continue;   // uniform across the CTA
-        if (!C) {
-            for (int r = threadIdx.x; r < d; r += kThreads) h1s[r] = H1[(int64_t)r * m + i];
-            __syncthreads();
-        }
-        for (int64_t j0 = 0; j0 < p; j0 += kThreads) {
+        for (int r = threadIdx.x; r < d; r += kThreads) h1s[r] = H1[(int64_t)r * m + i];
+        __syncthreads();
+        for (int64_t j0 = 0; j0 < p && off < end; j0 += kThreads) {
             const int64_t j = j0 + threadIdx.x;
             double e = 0.0;
             bool hit = false;
             if (j < p) {
-                e = C ? C[i * ldc + j] : estimate_at<D>(R, b, mask, h1s, H2, p, j, d, reduce);
-                hit = fabs(e) >= tau;
+                e = estimate_at<D>(R, b, mask, h1s, H2, p, j, d, reduce);
+                hit = hh_hit(e, hr);
             }
             const unsigned bal = __ballot_sync(0xffffffffu, hit);
             if (lane == 0) wcount[warp] = __popc(bal);
@@ -201,6 +252,104 @@ __global__ void __launch_bounds__(kThreads) hh_write_kernel(
             }
             off += total;
             __syncthreads();
+        }
+    }
+}
+
+// heavy hitters of a dense estimate, pass 1: hits per (row, tile), one warp
+// per tile (8 coalesced loads per lane)
+__global__ void __launch_bounds__(kThreads) hh_tile_count_kernel(const double *__restrict__ C,
+                                                                 int64_t ldc, int64_t m, int64_t p,
+                                                                 HhRange hr,
+                                                                 int32_t *__restrict__ tcounts,
+                                                                 int64_t ldt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nt = (p + kHhTile - 1) / kHhTile;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t item = w0; item < m * nt; item += nw) {
+        const int64_t i = item / nt, t = item % nt;
+        const double *row = C + i * ldc;
+        double e[kHhTile / 32];
+#pragma unroll
+        for (int u = 0; u < kHhTile / 32; ++u) {
+            const int64_t j = t * kHhTile + 32 * u + lane;
+            e[u] = j < p ? __ldcs(row + j) : 0.0;
+        }
+        int cnt = 0;
+#pragma unroll
+        for (int u = 0; u < kHhTile / 32; ++u)
+            cnt += __popc(__ballot_sync(0xffffffffu,
+                                        t * kHhTile + 32 * u + lane < p && hh_hit(e[u], hr)));
+        if (lane == 0) tcounts[i * ldt + t] = cnt;
+    }
+}
+
+// per row: tcounts[i][.] replaced by its inclusive prefix over the tiles,
+// counts[i] = the row total; one warp per row
+__global__ void __launch_bounds__(kThreads) hh_rowscan_kernel(int32_t *__restrict__ tcounts,
+                                                              int64_t ldt, int64_t m, int64_t nt,
+                                                              int64_t *__restrict__ counts) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < m; i += nw) {
+        int32_t *row = tcounts + i * ldt;
+        int carry = 0;   // a row holds at most p < 2^31 hits
+        for (int64_t t0 = 0; t0 < nt; t0 += 32) {
+            const int64_t t = t0 + lane;
+            int inc = t < nt ? row[t] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += v;
+            }
+            if (t < nt) row[t] = carry + inc;
+            carry += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        if (lane == 0) counts[i] = carry;
+    }
+}
+
+// pass 2: the hits of tile t of row i in column order, from offset
+// offsets[i] + (inclusive prefix of tile t - 1); one warp per (row, tile),
+// tiles without hits (equal prefixes) skipped after two loads
+__global__ void __launch_bounds__(kThreads) hh_tile_write_kernel(
+    const double *__restrict__ C, int64_t ldc, int64_t m, int64_t p, HhRange hr,
+    const int32_t *__restrict__ tinc, int64_t ldt, const int64_t *__restrict__ offsets,
+    int32_t *__restrict__ I, int32_t *__restrict__ J, double *__restrict__ V, int64_t capacity) {
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const int64_t nt = (p + kHhTile - 1) / kHhTile;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t item = w0; item < m * nt; item += nw) {
+        const int64_t i = item / nt, t = item % nt;
+        const int hi = tinc[i * ldt + t];
+        const int lo = t > 0 ? tinc[i * ldt + t - 1] : 0;
+        if (hi == lo) continue;
+        int64_t o = offsets[i] + lo;
+        const int64_t end = offsets[i + 1] < capacity ? offsets[i + 1] : capacity;
+        if (o >= end) continue;
+        const double *row = C + i * ldc;
+        double e[kHhTile / 32];
+#pragma unroll
+        for (int u = 0; u < kHhTile / 32; ++u) {
+            const int64_t j = t * kHhTile + 32 * u + lane;
+            e[u] = j < p ? __ldcs(row + j) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kHhTile / 32; ++u) {
+            const int64_t j = t * kHhTile + 32 * u + lane;
+            const bool hit = j < p && hh_hit(e[u], hr);
+            const unsigned bal = __ballot_sync(0xffffffffu, hit);
+            const int64_t pos = o + __popc(bal & below);
+            if (hit && pos < end) {
+                I[pos] = (int32_t)i;
+                J[pos] = (int32_t)j;
+                V[pos] = e[u];
+            }
+            o += __popc(bal);
         }
     }
 }
@@ -245,40 +394,94 @@ cudaError_t launch_hash_tables(const HashParams &hp, int d, int L, int64_t m, in
 #define CMM_ODD_D_CASES(X) X(1) X(3) X(5) X(7) X(9) X(11) X(13) X(15) X(17) X(19) X(21) X(23) \
     X(25) X(27) X(29) X(31) X(33)
 
+HhRange hh_range(double tau) {
+    HhRange hr;
+    hr.hi = 0x7ff0000000000000ull;   // +inf
+    if (tau != tau) {
+        hr.lo = 1;
+        hr.hi = 0;
+    } else if (tau <= 0.0) {
+        hr.lo = 0;
+    } else {
+        uint64_t bits;
+        std::memcpy(&bits, &tau, sizeof bits);
+        hr.lo = bits;
+    }
+    return hr;
+}
+
 template <bool CYC>
 cudaError_t launch_extract_t(const double *R, const uint32_t *H1, const uint32_t *H2, int d, int L,
                              int64_t m, int64_t p, int reduce, double *C, int64_t ldc, int64_t ldh,
-                             cudaStream_t s) {
+                             HhRange hr, int32_t *tcounts, int64_t ldt, cudaStream_t s) {
     const int64_t blocks = ((m + kRowsPerBlock - 1) / kRowsPerBlock) * ((p + kThreads - 1) / kThreads);
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     const unsigned g = (unsigned)blocks;
-    switch (d) {
-#define X(D) case D: extract_kernel<D, CYC><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh); break;
-        CMM_ODD_D_CASES(X)
+    if (tcounts) {
+        switch (d) {
+#define X(D) case D: extract_kernel<D, CYC, true><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh, hr, tcounts, ldt); break;
+            CMM_ODD_D_CASES(X)
 #undef X
-        default: extract_kernel<0, CYC><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh);
+            default: extract_kernel<0, CYC, true><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh, hr, tcounts, ldt);
+        }
+    } else {
+        switch (d) {
+#define X(D) case D: extract_kernel<D, CYC, false><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh, hr, tcounts, ldt); break;
+            CMM_ODD_D_CASES(X)
+#undef X
+            default: extract_kernel<0, CYC, false><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh, hr, tcounts, ldt);
+        }
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_extract(const double *R, const uint32_t *H1, const uint32_t *H2, int d, int L,
                            int64_t m, int64_t p, int reduce, double *C, int64_t ldc, int64_t ldh,
-                           cudaStream_t s, int cyclic) {
-    return cyclic ? launch_extract_t<true>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh, s)
-                  : launch_extract_t<false>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh, s);
+                           cudaStream_t s, int cyclic, HhRange hr, int32_t *tcounts, int64_t ldt) {
+    return cyclic ? launch_extract_t<true>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh, hr, tcounts,
+                                           ldt, s)
+                  : launch_extract_t<false>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh, hr, tcounts,
+                                            ldt, s);
 }
 
-cudaError_t launch_hh_count(const double *R, const uint32_t *H1, const uint32_t *H2,
-                            const double *C, int64_t ldc, int d, int L, int64_t m, int64_t p,
-                            int reduce, double tau, int64_t, int64_t, int64_t *counts,
+cudaError_t launch_hh_count(const double *R, const uint32_t *H1, const uint32_t *H2, int d, int L,
+                            int64_t m, int64_t p, int reduce, HhRange hr, int64_t *counts,
                             cudaStream_t s) {
     const unsigned g = clamp_grid(m);
-    switch (C ? -1 : d) {
-#define X(D) case D: hh_count_kernel<D><<<g, kThreads, 0, s>>>(R, H1, H2, C, ldc, d, L, m, p, reduce, tau, counts); break;
+    switch (d) {
+#define X(D) case D: hh_count_kernel<D><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, hr, counts); break;
         CMM_ODD_D_CASES(X)
 #undef X
-        default: hh_count_kernel<0><<<g, kThreads, 0, s>>>(R, H1, H2, C, ldc, d, L, m, p, reduce, tau, counts);
+        default: hh_count_kernel<0><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, hr, counts);
     }
+    return cudaGetLastError();
+}
+
+int64_t hh_tiles(int64_t p) { return (p + kHhTile - 1) / kHhTile; }
+
+cudaError_t launch_hh_tile_count(const double *C, int64_t ldc, int64_t m, int64_t p, HhRange hr,
+                                 int32_t *tcounts, int64_t ldt, cudaStream_t s) {
+    const int64_t items = m * hh_tiles(p);
+    const unsigned g = clamp_grid((items + kThreads / 32 - 1) / (kThreads / 32));
+    hh_tile_count_kernel<<<g, kThreads, 0, s>>>(C, ldc, m, p, hr, tcounts, ldt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hh_rowscan(int32_t *tcounts, int64_t ldt, int64_t m, int64_t p,
+                              int64_t *counts, cudaStream_t s) {
+    const unsigned g = clamp_grid((m + kThreads / 32 - 1) / (kThreads / 32));
+    hh_rowscan_kernel<<<g, kThreads, 0, s>>>(tcounts, ldt, m, hh_tiles(p), counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hh_tile_write(const double *C, int64_t ldc, int64_t m, int64_t p, HhRange hr,
+                                 const int32_t *tinc, int64_t ldt, const int64_t *offsets,
+                                 int32_t *I, int32_t *J, double *V, int64_t capacity,
+                                 cudaStream_t s) {
+    const int64_t items = m * hh_tiles(p);
+    const unsigned g = clamp_grid((items + kThreads / 32 - 1) / (kThreads / 32));
+    hh_tile_write_kernel<<<g, kThreads, 0, s>>>(C, ldc, m, p, hr, tinc, ldt, offsets, I, J, V,
+                                                capacity);
     return cudaGetLastError();
 }
 
@@ -288,16 +491,15 @@ cudaError_t launch_hh_scan(int64_t *counts, int64_t ntiles, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_hh_write(const double *R, const uint32_t *H1, const uint32_t *H2,
-                            const double *C, int64_t ldc, int d, int L, int64_t m, int64_t p,
-                            int reduce, double tau, int64_t, int64_t, const int64_t *offsets,
+cudaError_t launch_hh_write(const double *R, const uint32_t *H1, const uint32_t *H2, int d, int L,
+                            int64_t m, int64_t p, int reduce, HhRange hr, const int64_t *offsets,
                             int32_t *I, int32_t *J, double *V, int64_t capacity, cudaStream_t s) {
     const unsigned g = clamp_grid(m);
-    switch (C ? -1 : d) {
-#define X(D) case D: hh_write_kernel<D><<<g, kThreads, 0, s>>>(R, H1, H2, C, ldc, d, L, m, p, reduce, tau, offsets, I, J, V, capacity); break;
+    switch (d) {
+#define X(D) case D: hh_write_kernel<D><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, hr, offsets, I, J, V, capacity); break;
         CMM_ODD_D_CASES(X)
 #undef X
-        default: hh_write_kernel<0><<<g, kThreads, 0, s>>>(R, H1, H2, C, ldc, d, L, m, p, reduce, tau, offsets, I, J, V, capacity);
+        default: hh_write_kernel<0><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, hr, offsets, I, J, V, capacity);
     }
     return cudaGetLastError();
 }

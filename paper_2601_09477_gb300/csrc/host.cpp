@@ -240,14 +240,19 @@ int check_operands(const void *A, int64_t lda, int transA, const void *B, int64_
     return CMM_OK;
 }
 
+// extraction workspace: hash words of rows and columns, per-row counts and
+// offsets (2m + 1), per-(row, tile) counts of the dense heavy-hitter passes
 size_t extract_ws_bytes(int64_t m, int64_t p, int d) {
     return align_up((size_t)d * m * 4) + align_up((size_t)d * p * 4) +
-           align_up((size_t)(2 * m + 1) * sizeof(int64_t));
+           align_up((size_t)(2 * m + 1) * sizeof(int64_t)) +
+           align_up((size_t)m * hh_tiles(p) * sizeof(int32_t));
 }
 
 struct ExtractWs {
     uint32_t *H1, *H2;
     int64_t *counts;
+    int32_t *tcounts;   // m x nt, row stride nt
+    int64_t nt;
 };
 
 ExtractWs carve_extract(void *ws, int64_t m, int64_t p, int d) {
@@ -258,6 +263,9 @@ ExtractWs carve_extract(void *ws, int64_t m, int64_t p, int d) {
     e.H2 = reinterpret_cast<uint32_t *>(base);
     base += align_up((size_t)d * p * 4);
     e.counts = reinterpret_cast<int64_t *>(base);
+    base += align_up((size_t)(2 * m + 1) * sizeof(int64_t));
+    e.tcounts = reinterpret_cast<int32_t *>(base);
+    e.nt = hh_tiles(p);
     return e;
 }
 
@@ -295,27 +303,37 @@ int run_sketch(const void *A, int64_t lda, int transA, const void *B, int64_t ld
             e = cudaStreamWaitEvent(s, ready[c], 0);
             if (e != cudaSuccess) return cuda_fail(e, "wait for operand part");
         }
+        // this part's column maxima (the per-column scales of the fixed-point
+        // scatter): A^T rows, then B rows; taken by the preparation kernels
+        // where they run, else by a pass over the caller's FP32 rows
+        float *cm = colmax + 2 * k0;
+        const bool fx = prec != CMM_PREC_F64 && kp > 0;
+        if (fx && (pl.prep_A || pl.prep_B)) {
+            e = cudaMemsetAsync(cm, 0, 2 * kp * sizeof(float), s);
+            if (e != cudaSuccess) return cuda_fail(e, "column maxima reset");
+        }
         if (pl.prep_A && m > 0 && kp > 0) {
             Span sp("prep_A", s);
             // columns k0.. of A, or rows k0.. of A^T
             const char *Ap = static_cast<const char *>(A) + (transA ? k0 * lda : k0) * es;
-            e = launch_prep_A(Ap, lda, transA, dtype, prec, m, kp, At + k0 * pl.ldat * tb, pl.ldat, s);
+            e = launch_prep_A(Ap, lda, transA, dtype, prec, m, kp, At + k0 * pl.ldat * tb, pl.ldat, s,
+                              fx ? cm : nullptr);
             if (e != cudaSuccess) return cuda_fail(e, "prep A");
         }
         if (pl.prep_B && p > 0 && kp > 0) {
             Span sp("prep_B", s);
             e = launch_prep_B(static_cast<const char *>(B) + k0 * ldb * es, ldb, dtype, prec, kp, p,
-                              Bp + k0 * pl.ldbp * tb, pl.ldbp, s);
+                              Bp + k0 * pl.ldbp * tb, pl.ldbp, s, fx ? cm + kp : nullptr);
             if (e != cudaSuccess) return cuda_fail(e, "prep B");
         }
         const char *Atc = At + k0 * pl.ldat * tb;
         const char *Bpc = Bp + k0 * pl.ldbp * tb;
-        float *cm = colmax + 2 * k0;   // this part's maxima: A^T rows, then B rows
-        if (prec != CMM_PREC_F64) {
-            // the per-column scales of the fixed-point scatter
-            Span sp("colmax", s, 2);
-            e = launch_rowmax((const float *)Atc, pl.ldat, kp, m, cm, s);
-            if (e == cudaSuccess) e = launch_rowmax((const float *)Bpc, pl.ldbp, kp, p, cm + kp, s);
+        if (fx && !(pl.prep_A && pl.prep_B)) {
+            Span sp("colmax", s, (pl.prep_A || pl.prep_B) ? 1 : 2);
+            e = cudaSuccess;
+            if (!pl.prep_A) e = launch_rowmax((const float *)Atc, pl.ldat, kp, m, cm, s);
+            if (e == cudaSuccess && !pl.prep_B)
+                e = launch_rowmax((const float *)Bpc, pl.ldbp, kp, p, cm + kp, s);
             if (e != cudaSuccess) return cuda_fail(e, "column maxima");
         }
         SketchPlan pp = pl;   // this part's blocks
@@ -351,8 +369,12 @@ int run_sketch(const void *A, int64_t lda, int transA, const void *B, int64_t ld
     return CMM_OK;
 }
 
+// Decompress into C.  With hr non-null the extraction also counts, per row
+// and column tile, the estimates that pass the heavy-hitter test (into the
+// workspace's tile counts) for finish_hh.
 int run_extract(const double *R, const cmm_hashes *hs, int64_t m, int64_t p, int reduce,
-                double *C, int64_t ldc, void *ws, cudaStream_t s, int cyclic = 0) {
+                double *C, int64_t ldc, void *ws, cudaStream_t s, int cyclic = 0,
+                const HhRange *hr = nullptr) {
     if (m == 0 || p == 0) return CMM_OK;
     HashParams hp;
     fill_params(hs, hp);
@@ -365,56 +387,72 @@ int run_extract(const double *R, const cmm_hashes *hs, int64_t m, int64_t p, int
     if (e != cudaSuccess) return cuda_fail(e, "hash tables");
     {
         Span sp("extract", s);
-        e = launch_extract(R, ew.H1, ew.H2, hs->d, hs->log2b, m, p, reduce, C, ldc, m, s, cyclic);
+        e = launch_extract(R, ew.H1, ew.H2, hs->d, hs->log2b, m, p, reduce, C, ldc, m, s, cyclic,
+                           hr ? *hr : HhRange{1, 0}, hr ? ew.tcounts : nullptr, ew.nt);
     }
     if (e != cudaSuccess) return cuda_fail(e, "extract kernel");
     return CMM_OK;
 }
 
+// The heavy-hitter list, given per-(row, tile) counts in ew.tcounts (dense C)
+// or per-row counts in ew.counts (from R): row sums, a scan into offsets, each
+// row's hits written in column order (rows past `capacity` are skipped on the
+// device), then the total is read.  One host synchronisation, at the end.
+int finish_hh(const double *R, const ExtractWs &ew, const double *C, int64_t ldc, int64_t m,
+              int64_t p, int d, int L, int reduce, HhRange hr, int32_t *I, int32_t *J, double *V,
+              int64_t capacity, int64_t *count, cudaStream_t s) {
+    cudaError_t e;
+    {
+        Span sp("hh_scan", s, C ? 2 : 1);
+        e = C ? launch_hh_rowscan(ew.tcounts, ew.nt, m, p, ew.counts, s) : cudaSuccess;
+        if (e == cudaSuccess) e = launch_hh_scan(ew.counts, m, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter scan");
+    if (capacity > 0) {
+        Span sp(C ? "hh_write_dense" : "hh_write", s);
+        e = C ? launch_hh_tile_write(C, ldc, m, p, hr, ew.tcounts, ew.nt, ew.counts + m, I, J, V,
+                                     capacity, s)
+              : launch_hh_write(R, ew.H1, ew.H2, d, L, m, p, reduce, hr, ew.counts + m, I, J, V,
+                                capacity, s);
+        if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter write");
+    }
+    int64_t total = 0;
+    e = cudaMemcpyAsync(&total, ew.counts + 2 * m, sizeof total, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter count copy");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter sync");
+    *count = total;
+    if (total > capacity)
+        return fail(CMM_ERR_CAPACITY, "%lld heavy hitters, capacity %lld", (long long)total,
+                    (long long)capacity);
+    return CMM_OK;
+}
+
+// heavy hitters of the dense C (hs null) or of the estimates from R
 int run_hh(const double *R, const cmm_hashes *hs, const double *C, int64_t ldc, int64_t m,
            int64_t p, int d, int L, int reduce, double tau, int32_t *I, int32_t *J, double *V,
            int64_t capacity, int64_t *count, void *ws, cudaStream_t s) {
     *count = 0;
     if (m == 0 || p == 0) return CMM_OK;
     ExtractWs ew = carve_extract(ws, m, p, d);
+    const HhRange hr = hh_range(tau);
     cudaError_t e;
-    if (!C) {
+    if (C) {
+        Span sp("hh_count_dense", s);
+        e = launch_hh_tile_count(C, ldc, m, p, hr, ew.tcounts, ew.nt, s);
+    } else {
         HashParams hp;
         fill_params(hs, hp);
-        Span sp("hash_tables", s);
-        e = launch_hash_tables(hp, d, L, m, p, ew.H1, ew.H2, s);
+        {
+            Span sp("hash_tables", s);
+            e = launch_hash_tables(hp, d, L, m, p, ew.H1, ew.H2, s);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "hash tables");
-    }
-    {
-        Span sp(C ? "hh_count_dense" : "hh_count", s);
-        e = launch_hh_count(R, ew.H1, ew.H2, C, ldc, d, L, m, p, reduce, tau, 1, m, ew.counts, s);
+        Span sp("hh_count", s);
+        e = launch_hh_count(R, ew.H1, ew.H2, d, L, m, p, reduce, hr, ew.counts, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter count");
-    {
-        Span sp("hh_scan", s);
-        e = launch_hh_scan(ew.counts, m, s);
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter scan");
-    int64_t total = 0;
-    e = cudaMemcpyAsync(&total, ew.counts + 2 * m, sizeof total, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter count copy");
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter count sync");
-    *count = total;
-    if (total > 0 && capacity > 0) {
-        {
-            Span sp(C ? "hh_write_dense" : "hh_write", s);
-            e = launch_hh_write(R, ew.H1, ew.H2, C, ldc, d, L, m, p, reduce, tau, 1, m,
-                                ew.counts + m, I, J, V, capacity, s);
-        }
-        if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter write");
-        e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter write sync");
-    }
-    if (total > capacity)
-        return fail(CMM_ERR_CAPACITY, "%lld heavy hitters, capacity %lld", (long long)total,
-                    (long long)capacity);
-    return CMM_OK;
+    return finish_hh(R, ew, C, ldc, m, p, d, L, reduce, hr, I, J, V, capacity, count, s);
 }
 
 // ---- adjoint planning --------------------------------------------------------
@@ -779,6 +817,42 @@ int cmm_multiply(const void *A, int64_t lda, int32_t transA, const void *B, int6
     return run_extract(Rw, hs, m, p, reduce, C, ldc, scratch, s);
 }
 
+int cmm_multiply_threshold(const void *A, int64_t lda, int32_t transA, const void *B, int64_t ldb,
+                           int32_t dtype, int64_t m, int64_t k, int64_t p, const cmm_hashes *hs,
+                           int32_t prec, int32_t reduce, double *C, int64_t ldc, double *R,
+                           double tau, int32_t *I, int32_t *J, double *V, int64_t capacity,
+                           int64_t *count, void *ws, size_t ws_bytes, void *stream) {
+    g_err.clear();
+    if (!count) return fail(CMM_ERR_ARG, "count is NULL");
+    *count = 0;
+    if (capacity < 0) return fail(CMM_ERR_ARG, "negative capacity");
+    if (capacity > 0 && (!I || !J || !V)) return fail(CMM_ERR_ARG, "I, J or V is NULL");
+    int rc = check_hashes(hs);
+    if (rc) return rc;
+    rc = check_operands(A, lda, transA, B, ldb, dtype, m, k, p, prec);
+    if (rc) return rc;
+    if (prec == CMM_PREC_BF16TC && hs->log2b < sketch_bf16_llo())
+        return fail(CMM_ERR_RANGE, "precision BF16TC needs log2b >= %d", sketch_bf16_llo());
+    if (reduce != CMM_MEDIAN && reduce != CMM_MEAN) return fail(CMM_ERR_ARG, "bad reduce %d", reduce);
+    if (m > 0 && p > 0 && (!C || ldc < p)) return fail(CMM_ERR_ARG, "C is NULL or ldc < p");
+    const size_t need = cmm_multiply_workspace_bytes(m, k, p, hs->d, hs->log2b, dtype, prec, transA);
+    rc = check_ws(ws, ws_bytes, need);
+    if (rc) return rc;
+    char *base = static_cast<char *>(ws);
+    const size_t rbytes = align_up((size_t)hs->d * (size_t(1) << hs->log2b) * sizeof(double));
+    double *Rw = R ? R : reinterpret_cast<double *>(base);
+    void *scratch = base + rbytes;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    rc = run_sketch(A, lda, transA, B, ldb, dtype, m, k, p, hs, prec, Rw, scratch, s);
+    if (rc) return rc;
+    if (m == 0 || p == 0) return CMM_OK;
+    const HhRange hr = hh_range(tau);
+    rc = run_extract(Rw, hs, m, p, reduce, C, ldc, scratch, s, 0, &hr);
+    if (rc) return rc;
+    return finish_hh(nullptr, carve_extract(scratch, m, p, hs->d), C, ldc, m, p, hs->d,
+                     hs->log2b, reduce, hr, I, J, V, capacity, count, s);
+}
+
 namespace {
 
 // ---- the host-buffer path: copies overlapped with the computation ----------
@@ -870,6 +944,8 @@ int cmm_multiply_host(const void *A, int64_t lda, int32_t transA, const void *B,
     if (count && capacity < 0) return fail(CMM_ERR_ARG, "negative capacity");
     if (count && capacity > 0 && (!I || !J || !V)) return fail(CMM_ERR_ARG, "I, J or V is NULL");
     const int64_t cap = count ? capacity : 0;
+    if (count) *count = 0;
+    const HhRange hr = hh_range(tau);
     const size_t need = cmm_multiply_host_workspace_bytes(m, k, p, hs->d, hs->log2b, dtype, prec,
                                                           transA, cap);
     rc = check_ws(ws, ws_bytes, need);
@@ -951,7 +1027,8 @@ int cmm_multiply_host(const void *A, int64_t lda, int32_t transA, const void *B,
             {
                 Span sp("extract", s);
                 e = launch_extract(Rw, ew.H1 + i0, ew.H2, hs->d, hs->log2b, mb, p, reduce,
-                                   dC + i0 * p, p, m, s);
+                                   dC + i0 * p, p, m, s, 0, hr,
+                                   count ? ew.tcounts + i0 * ew.nt : nullptr, ew.nt);
             }
             if (e != cudaSuccess) return cuda_fail(e, "extract kernel");
             if (C) {
@@ -967,9 +1044,9 @@ int cmm_multiply_host(const void *A, int64_t lda, int32_t transA, const void *B,
         }
     }
     int hh_rc = CMM_OK;
-    if (count) {
-        hh_rc = run_hh(nullptr, nullptr, dC, p, m, p, 1, 1, CMM_MEDIAN, tau, dI, dJ, dV, cap, count,
-                       scratch, s);
+    if (count && m > 0 && p > 0) {
+        hh_rc = finish_hh(nullptr, carve_extract(scratch, m, p, hs->d), dC, p, m, p, hs->d,
+                          hs->log2b, reduce, hr, dI, dJ, dV, cap, count, s);
         if (hh_rc != CMM_OK && hh_rc != CMM_ERR_CAPACITY) return hh_rc;
         const int64_t n = std::min(*count, cap);
         if (n > 0) {
