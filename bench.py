@@ -91,6 +91,31 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
+def alu_roofline(kernel: str, ops: float, ms: float, note: str = "") -> dict:
+    """Roofline object of an FP32-ALU-bound kernel: algorithmic operations per
+    launch / its average launch time, against 152 SMs x 128 FP32 lanes at the
+    maximum SM clock."""
+    _, _, pk = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    peak = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    achieved = ops / (ms * 1e-3) / 1e12
+    out = {"bound": "alu", "kernel": kernel, "achieved": round(achieved, 3),
+           "peak": round(peak, 3), "unit": "Tops/s", "frac": round(achieved / peak, 4),
+           "traffic": None, "ops_per_launch": ops,
+           "peak_source": "152 SMs x 128 FP32 lanes x %g MHz max SM clock" % sm_max,
+           "avg_launch_ms": round(ms, 4)}
+    if note:
+        out["ops_counted"] = note
+    return out
+
+
+def timed_oracle(fn) -> float:
+    """Seconds one call of an oracle function takes on the host cores."""
+    t0 = time.perf_counter()
+    fn()
+    return time.perf_counter() - t0
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling while the timed region runs."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -179,8 +204,13 @@ def oracle_sample(A, B, hp, log2b, n, d, tau, k_sample, rows_sample, threads):
     orc.extract(R, hp, n, n, rows=(0, rows_sample), nthreads=threads)
     t2 = time.perf_counter()
     ms = ((t1 - t0) * n / k_sample + (t2 - t1) * n / rows_sample) * 1e3
-    sample = ("Compress on %d of %d inner indices, Decompress of %d of %d rows, FP64, %d threads; "
-              "scaled linearly to the full step" % (k_sample, n, rows_sample, n, threads))
+    if k_sample == n and rows_sample == n:
+        sample = ("the whole step: Compress over all %d inner indices and Decompress of all %d "
+                  "rows, FP64, %d threads (no scaling)" % (n, n, threads))
+    else:
+        sample = ("Compress on %d of %d inner indices, Decompress of %d of %d rows, FP64, %d "
+                  "threads; scaled linearly to the full step" % (k_sample, n, rows_sample, n,
+                                                                threads))
     return ms, sample, (t2 - t0)
 
 
@@ -400,8 +430,8 @@ def run_cmm(a):
     if not a.no_cpu and rank == 0 and world == 1:
         from oracle import oracle as orc
         threads = orc.max_threads()
-        cpu_ms, sample, secs = oracle_sample(A_np, B_np, h.params, L, n, d, tau,
-                                             max(16, n // 4), max(16, n // 16), threads)
+        # the whole step at the benchmark size takes the oracle about 5 s on 16 cores
+        cpu_ms, sample, secs = oracle_sample(A_np, B_np, h.params, L, n, d, tau, n, n, threads)
         result["cpu_baseline"] = {"value": round(cpu_ms, 1), "unit": "ms", "cores": threads,
                                   "kind": "oracle", "sample": sample,
                                   "sample_seconds": round(secs, 2)}
@@ -452,13 +482,21 @@ def run_batched(a):
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
             batch.launch()
+        clocks = ClockSampler(0)
+        clocks.start()
         ms = _events_ms(g.replay, a.steps)
+        out[label + "_clocks"] = clocks.stop()
         assert batch.status() == cmm.OK
         out[label + "_ms"] = round(ms, 3)
     flops = sum(d * pb.At.shape[0] * (2.0 * (1 << pb.hashes.log2b) * pb.hashes.log2b +
                                       (1 << pb.hashes.log2b)) for pb in probs)
     outputs = sum(pb.At.shape[1] * pb.B.shape[1] for pb in probs)
     best = min(out["default_ms"], out["tuned_ms"])
+    out["roofline"] = alu_roofline("batched_kernel", flops, best,
+                                   "per problem d*k*(2 b log2 b + b): butterflies of both "
+                                   "sketches and the MAC")
+    if not a.no_cpu:
+        out["cpu_baseline"] = batched_oracle(raw, probs, d, nsample=32)
     res = {"metric": "batched: 256 uneven problems (sketch + FP64 finish + median extraction), "
                      "one persistent launch replayed from a CUDA graph, ms",
            "value": best, "unit": "ms", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
@@ -470,6 +508,38 @@ def run_batched(a):
     res.update(out)
     print(json.dumps(res), flush=True)
     return 0
+
+
+def batched_oracle(raw, probs, d, nsample=8):
+    """FP64 oracle (Compress + Decompress of every entry) on the first nsample
+    problems of the batch, scaled to all of them: Compress time by the ratio of
+    d*k*b*log2 b, Decompress time by the ratio of d*m*p."""
+    from oracle import oracle as orc
+    threads = orc.max_threads()
+    tc = te = 0.0
+    cs = es = 0.0
+    for q in range(nsample):
+        At, B, L, _ = raw[q]
+        At64 = At.double().cpu().numpy()
+        B64 = B.double().cpu().numpy()
+        hp = probs[q].hashes.params
+        m, p = At64.shape[1], B64.shape[1]
+        box = {}
+        tc += timed_oracle(lambda: box.setdefault("R", orc.compress(At64, B64, hp, L, transA=True,
+                                                                    nthreads=threads)))
+        te += timed_oracle(lambda: orc.extract(box["R"], hp, m, p, nthreads=threads))
+    def ccost(pb):
+        return d * pb.At.shape[0] * (1 << pb.hashes.log2b) * pb.hashes.log2b
+    def ecost(pb):
+        return d * pb.At.shape[1] * pb.B.shape[1]
+    cs = sum(ccost(pb) for pb in probs[:nsample])
+    es = sum(ecost(pb) for pb in probs[:nsample])
+    ms = (tc * sum(ccost(pb) for pb in probs) / cs + te * sum(ecost(pb) for pb in probs) / es) * 1e3
+    return {"value": round(ms, 1), "unit": "ms", "cores": threads, "kind": "oracle",
+            "sample": "Compress + Decompress of the first %d of %d problems, FP64, %d threads; "
+                      "scaled by d*k*b*log2 b (Compress) and d*m*p (Decompress)"
+                      % (nsample, len(probs), threads),
+            "sample_seconds": round(tc + te, 2)}
 
 
 def run_precision(a):
@@ -485,14 +555,21 @@ def run_precision(a):
     ws = torch.empty(max(cmm.multiply_workspace_bytes(n, n, n, h, torch.float32, p)
                          for p in ("f32", "bf16tc", "f64")), dtype=torch.uint8, device="cuda")
     C = torch.empty((n, n), dtype=torch.float64, device="cuda")
-    Rs, times = {}, {}
+    Rs, times, kernels = {}, {}, {}
+    clocks = ClockSampler(0)
+    clocks.start()
     for prec, reps in (("f64", 1), ("f32", a.steps), ("bf16tc", a.steps)):
         R = torch.empty((d, 1 << L), dtype=torch.float64, device="cuda")
         fn = lambda: cmm.multiply(A, B, h, prec=prec, R=R, out=C, ws=ws)
         for _ in range(1 if prec == "f64" else a.warmup):
             fn()
+        torch.cuda.synchronize()
+        cmm.trace_enable(True)
         times[prec] = round(_events_ms(fn, reps), 3)
+        cmm.trace_enable(False)
+        kernels[prec] = {k: round(v[1] / reps, 4) for k, v in cmm.trace_read().items()}
         Rs[prec] = R
+    clk = clocks.stop()
     scale = float((torch.linalg.vector_norm(A.double(), dim=0) *
                    torch.linalg.vector_norm(B.double(), dim=1)).sum().item())
     err = {p: float((Rs[p] - Rs["f64"]).abs().max().item() / scale) for p in ("f32", "bf16tc")}
@@ -505,7 +582,28 @@ def run_precision(a):
            "ms": times, "R_err_rel_to_sum_norms": err,
            "R_err_rel_to_rms": {p: float((Rs[p] - Rs["f64"]).abs().max().item() / rms)
                                 for p in ("f32", "bf16tc")},
-           "speedup_vs_fp64": {p: round(times["f64"] / times[p], 2) for p in ("f32", "bf16tc")}}
+           "speedup_vs_fp64": {p: round(times["f64"] / times[p], 2) for p in ("f32", "bf16tc")},
+           "kernels_ms_per_call": kernels, "clocks": clk,
+           "roofline": alu_roofline("sketch_f32", d * n * (2.0 * (1 << L) * L + (1 << L)),
+                                    kernels["f32"].get("sketch_f32", float("nan")),
+                                    "d*k*(2 b log2 b + b)")}
+    if not a.no_cpu:
+        from oracle import oracle as orc
+        threads = orc.max_threads()
+        ks, rows = 2048, 64
+        A64 = A[:, :ks].double().cpu().numpy()
+        B64 = B[:ks].double().cpu().numpy()
+        box = {}
+        tc = timed_oracle(lambda: box.setdefault("R", orc.compress(A64, B64, h.params, L,
+                                                                   nthreads=threads)))
+        te = timed_oracle(lambda: orc.extract(box["R"], h.params, n, n, rows=(0, rows),
+                                              nthreads=threads))
+        res["cpu_baseline"] = {
+            "value": round((tc * n / ks + te * n / rows) * 1e3, 1), "unit": "ms",
+            "cores": threads, "kind": "oracle",
+            "sample": "Compress over %d of %d inner indices, Decompress of %d of %d rows, FP64, "
+                      "%d threads; scaled linearly to one multiply" % (ks, n, rows, n, threads),
+            "sample_seconds": round(tc + te, 2)}
     print(json.dumps(res), flush=True)
     return 0
 
@@ -533,15 +631,44 @@ def run_diff(a):
 
     for _ in range(a.warmup):
         fwd_bwd()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
     with torch.no_grad():
         f_ms = _events_ms(fwd, a.steps)
+    cmm.trace_enable(True)
     fb_ms = _events_ms(fwd_bwd, a.steps)
+    cmm.trace_enable(False)
+    clk = clocks.stop()
+    kernels = {k: round(v[1] / a.steps, 4) for k, v in cmm.trace_read().items()}
+    n, L, d = 4096, 14, 5
+    fwd_ops = d * n * (2.0 * (1 << L) * L + (1 << L))
+    adj_ops = d * n * (4.0 * (1 << L) * L + 2.0 * (1 << L))
     res = {"metric": "differentiation: forward and forward+backward ms (mean estimator, autograd)",
            "value": round(fb_ms, 3), "unit": "ms", "n_gpus": 1, "steps": a.steps,
            "warmup": a.warmup, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "n=4096 FP32, N(0,1)/sqrt(n) + 256 spikes, b=2^14, d=5, "
                                   "loss over 4096 weighted pairs"},
-           "forward_ms": round(f_ms, 3), "forward_backward_ms": round(fb_ms, 3)}
+           "forward_ms": round(f_ms, 3), "forward_backward_ms": round(fb_ms, 3),
+           "kernels_ms_per_step": kernels, "clocks": clk,
+           "roofline": alu_roofline("adjoint_f32", adj_ops, kernels.get("adjoint_f32", float("nan")),
+                                    "d*k*(4 b log2 b + 2 b): per (r, t) the transforms of x_t "
+                                    "and y_t, their products with H G and the inverse transforms"),
+           "roofline_forward": alu_roofline("sketch_f32", fwd_ops,
+                                            kernels.get("sketch_f32", float("nan")),
+                                            "d*k*(2 b log2 b + b)")}
+    if not a.no_cpu:
+        from oracle import oracle as orc
+        threads = orc.max_threads()
+        box = {}
+        tf = timed_oracle(lambda: box.setdefault("y", orc.mean_at_pairs(
+            orc.compress(A, B, h.params, L, nthreads=threads), h.params, I, J)))
+        tb = timed_oracle(lambda: orc.adjoint(A, B, h.params, L, I, J, W))
+        res["cpu_baseline"] = {
+            "value": round((tf + tb) * 1e3, 1), "unit": "ms", "cores": threads, "kind": "oracle",
+            "sample": "the whole forward (Compress + mean at the 4096 pairs, %d threads) and "
+                      "backward (adjoint through dense M, numpy BLAS) once, FP64" % threads,
+            "forward_ms": round(tf * 1e3, 1), "backward_ms": round(tb * 1e3, 1)}
     print(json.dumps(res), flush=True)
     return 0
 
@@ -567,6 +694,8 @@ def run_cyclic(a):
     tau = 0.5 * n
     pl = pairs.tolist()
     planted = {(int(i), int(j)) for i, j in pl} | {(int(j), int(i)) for i, j in pl}
+    clocks = ClockSampler(0)
+    clocks.start()
     for name, fn in forms.items():
         for _ in range(a.warmup):
             fn()
@@ -585,7 +714,27 @@ def run_cyclic(a):
            "config": {"workload": "planted +-1 correlations n=%d (64 pairs, rho=0.9, B=A^T, FP32 "
                                   "storage), b=2^%d, d=%d" % (n, L, d)},
            "ms": times, "fft_over_fwht": round(times["cyclic"] / times["fwht"], 2),
-           "kernels_ms_per_step": kernels, "planted_recall": recall}
+           "kernels_ms_per_step": kernels, "planted_recall": recall, "clocks": clocks.stop(),
+           "roofline": alu_roofline("sketch_cyclic", d * n * (5.0 * (1 << L) * L + 4.0 * (1 << L)),
+                                    kernels["cyclic"].get("sketch_cyclic", float("nan")),
+                                    "d*k*(5 b log2 b + 4 b): two real-input FFTs of length b "
+                                    "(2.5 b log2 b flops each) and the complex multiply-add of "
+                                    "b/2 bins, per (r, t)")}
+    if not a.no_cpu:
+        from oracle import oracle as orc
+        ks, rows = 128, 64
+        A64 = A[:, :ks].double().cpu().numpy()
+        B64 = B[:ks].double().cpu().numpy()
+        box = {}
+        tc = timed_oracle(lambda: box.setdefault("R", orc.compress_cyclic(A64, B64, h.params, L)))
+        te = timed_oracle(lambda: orc.extract_cyclic(box["R"], h.params, n, n, rows=(0, rows)))
+        res["cpu_baseline"] = {
+            "value": round((tc * n / ks + te * n / rows) * 1e3, 1), "unit": "ms", "cores": 1,
+            "kind": "oracle",
+            "sample": "cyclic Compress (numpy FFT) over %d of %d inner indices, Decompress of %d "
+                      "of %d rows, FP64, one thread; scaled linearly to one multiply"
+                      % (ks, n, rows, n),
+            "sample_seconds": round(tc + te, 2)}
     print(json.dumps(res), flush=True)
     return 0
 
@@ -626,6 +775,28 @@ def run_instances(a):
            "higher_is_better": False, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "Logunit, Diagonal, Covariance, Lightbulb generators, n=4096, "
                                   "FP64 storage"}, "rows": rows}
+    if not a.no_cpu:
+        # the oracle on the first row's instance: Compress over ks of the n inner
+        # indices and Decompress of `nr` rows, scaled linearly to one multiply
+        from oracle import oracle as orc
+        threads = orc.max_threads()
+        name, cd, cb = "logunit", 1.0, 0.5
+        d, L = ev.params(n, cd, cb)
+        A, B, _, _ = ev.instance(name, n, seed=1)
+        hp = cmm.make_hashes(7, d, L).params
+        ks, nr = 1024, 256
+        A64 = A[:, :ks].double().cpu().numpy()
+        B64 = B[:ks].double().cpu().numpy()
+        box = {}
+        tc = timed_oracle(lambda: box.setdefault("R", orc.compress(A64, B64, hp, L,
+                                                                   nthreads=threads)))
+        te = timed_oracle(lambda: orc.extract(box["R"], hp, n, n, rows=(0, nr), nthreads=threads))
+        res["cpu_baseline"] = {
+            "value": round((tc * n / ks + te * n / nr) * 1e3, 1), "unit": "ms", "cores": threads,
+            "kind": "oracle", "instance": "%s c_d=%g c_b=%g (d=%d, b=2^%d)" % (name, cd, cb, d, L),
+            "sample": "Compress over %d of %d inner indices, Decompress of %d of %d rows, FP64, "
+                      "%d threads; scaled linearly to one multiply" % (ks, n, nr, n, threads),
+            "sample_seconds": round(tc + te, 2)}
     print(json.dumps(res), flush=True)
     return 0
 
