@@ -44,7 +44,7 @@ constexpr int kFinishLlo = 12;   // FP64 slice of the inverse transform: 2^12 do
 
 // Most parts a sketch is split into along the inner index (the host-buffer
 // path sketches part c while part c + 1 is still being copied).
-constexpr int kMaxParts = 2;
+constexpr int kMaxParts = 4;
 
 // Plan of one cmm_sketch call.
 struct SketchPlan {

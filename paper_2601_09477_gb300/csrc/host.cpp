@@ -2,6 +2,7 @@
 // parameter generation, workspace planning and kernel launches.  No function
 // here allocates device memory; every scratch byte comes from the caller's ws.
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -135,8 +136,11 @@ bool use_tmem_kernel() {
 }
 
 // ---- sketch planning -------------------------------------------------------
+// nparts > 1 splits the inner index into parts (the host-buffer path): part
+// c holds a share of k proportional to ratio^c (ratio <= 0: equal parts)
 bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int prec, int transA,
-                 int64_t lda, int64_t ldb, SketchPlan &pl, int nparts = 1) {
+                 int64_t lda, int64_t ldb, SketchPlan &pl, int nparts = 1,
+                 double ratio = 0.0) {
     pl = SketchPlan{};
     pl.prec = prec;
     pl.L = L;
@@ -168,7 +172,18 @@ bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int p
     if (k < nparts) nparts = 1;
     pl.nparts = nparts;
     pl.nchunks = 0;
-    for (int c = 0; c <= nparts; ++c) pl.kb[c] = k * c / nparts;
+    if (ratio > 0.0 && nparts > 1) {
+        double w[kMaxParts + 1] = {0.0};
+        for (int c = 0; c < nparts; ++c) w[c + 1] = w[c] + std::pow(ratio, c);
+        pl.kb[0] = 0;
+        for (int c = 1; c < nparts; ++c)
+            pl.kb[c] = std::min<int64_t>(k - (nparts - c),
+                                         std::max<int64_t>(pl.kb[c - 1] + 1,
+                                                           (int64_t)(k * w[c] / w[nparts])));
+        pl.kb[nparts] = k;
+    } else {
+        for (int c = 0; c <= nparts; ++c) pl.kb[c] = k * c / nparts;
+    }
     for (int c = 0; c < nparts; ++c) {
         const int64_t kk = std::max<int64_t>(pl.kb[c + 1] - pl.kb[c], 1);
         const int64_t nc_min = std::max<int64_t>(1, (kk + 256 * G - 1) / (256 * G));
@@ -274,9 +289,10 @@ ExtractWs carve_extract(void *ws, int64_t m, int64_t p, int d) {
 // given), so a producer on another stream may still be filling later parts.
 int run_sketch(const void *A, int64_t lda, int transA, const void *B, int64_t ldb, int dtype,
                int64_t m, int64_t k, int64_t p, const cmm_hashes *hs, int prec, double *R,
-               void *ws, cudaStream_t s, int nparts = 1, const cudaEvent_t *ready = nullptr) {
+               void *ws, cudaStream_t s, int nparts = 1, const cudaEvent_t *ready = nullptr,
+               double ratio = 0.0) {
     SketchPlan pl;
-    plan_sketch(m, k, p, hs->d, hs->log2b, dtype, prec, transA, lda, ldb, pl, nparts);
+    plan_sketch(m, k, p, hs->d, hs->log2b, dtype, prec, transA, lda, ldb, pl, nparts, ratio);
     HashParams hp;
     fill_params(hs, hp);
     char *base = static_cast<char *>(ws);
@@ -856,25 +872,52 @@ int cmm_multiply_threshold(const void *A, int64_t lda, int32_t transA, const voi
 namespace {
 
 // ---- the host-buffer path: copies overlapped with the computation ----------
-// The inner index is split in two parts when the operands are large: part 1
-// is copied to the device on an internal copy stream while part 0 is
-// prepared and sketched on the caller's stream.  The estimate is extracted in
-// row blocks, each copied back while the next is extracted.
-constexpr int kHostRowBlocks = 4;
+// The inner index is split in up to four parts when the operands are large:
+// part c + 1 is copied to the device on an internal copy stream while part c
+// is prepared and sketched on the caller's stream.  The estimate is extracted
+// in row blocks, each copied back while the next is extracted.
+constexpr int kHostRowBlocks = 8;   // at most; one per 16 MiB of the estimate
 
+// operands of 64 MiB or more: two parts; 256 MiB or more: three; 1 GiB or
+// more: four (every part at least 512 inner indices)
 int host_parts(int64_t m, int64_t k, int64_t p, size_t es) {
-    return (k >= 512 && (double)(m + p) * (double)k * (double)es >= 64.0 * 1048576.0) ? 2 : 1;
+    const double bytes = (double)(m + p) * (double)k * (double)es;
+    if (k < 512 || bytes < 64.0 * 1048576.0) return 1;
+    if (bytes >= 1024.0 * 1048576.0 && k >= 4 * 512) return 4;
+    return bytes >= 256.0 * 1048576.0 && k >= 3 * 512 ? 3 : 2;
 }
 
+// Ratio of the parts' sizes along the inner index: while part c is sketched
+// part c + 1 is copied, so neither waits when part c + 1 is `ratio` times part
+// c, ratio = sketch time / copy time per inner index.  Per inner index the
+// copy moves (m + p) elements over the host link (~211 GB/s measured on this
+// GPU's host path) and the sketch does d (2 b log2 b + b) butterfly
+// operations (~18 Tops/s FP32, ~13 Tops/s BF16 blocks, ~0.45 Tops/s FP64).
+// Kept within [1/2, 3]: only the first part's copy is exposed, and it shrinks
+// as the later parts grow.
+double host_part_ratio(int64_t m, int64_t p, int d, int L, size_t es, int prec) {
+    const double b = std::ldexp(1.0, L);
+    const double copy_t = (double)(m + p) * (double)es / 211e9;
+    const double rate = prec == CMM_PREC_F64 ? 0.45e12 : prec == CMM_PREC_BF16TC ? 13e12 : 18e12;
+    const double sketch_t = (double)d * (2.0 * b * L + b) / rate;
+    return std::min(3.0, std::max(0.5, sketch_t / copy_t));
+}
+
+// row blocks of the estimate: one per 16 MiB (at most kHostRowBlocks, at
+// least 256 rows each), so that only the last block's copy is left exposed
 int host_row_blocks(int64_t m, int64_t p) {
-    return (m >= 4 * 256 && (double)m * (double)p * 8.0 >= 32.0 * 1048576.0) ? kHostRowBlocks : 1;
+    const double bytes = (double)m * (double)p * 8.0;
+    int nrb = (int)std::min<double>(kHostRowBlocks, std::floor(bytes / (16.0 * 1048576.0)));
+    while (nrb > 1 && m < (int64_t)nrb * 256) --nrb;
+    return std::max(1, nrb);
 }
 
 size_t host_sketch_ws(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int prec,
                       int transA) {
     SketchPlan pl;
     if (!plan_sketch(m, k, p, d, L, dtype, prec, transA, transA ? m : k, p, pl,
-                     host_parts(m, k, p, dtype_size(dtype))))
+                     host_parts(m, k, p, dtype_size(dtype)),
+                     host_part_ratio(m, p, d, L, dtype_size(dtype), prec)))
         return 0;
     return pl.total;
 }
@@ -984,7 +1027,9 @@ int cmm_multiply_host(const void *A, int64_t lda, int32_t transA, const void *B,
     // device copy is compact)
     SketchPlan pl;
     const int nparts = host_parts(m, k, p, es);
-    plan_sketch(m, k, p, hs->d, hs->log2b, dtype, prec, transA, transA ? m : k, p, pl, nparts);
+    const double ratio = host_part_ratio(m, p, hs->d, hs->log2b, es, prec);
+    plan_sketch(m, k, p, hs->d, hs->log2b, dtype, prec, transA, transA ? m : k, p, pl, nparts,
+                ratio);
     const int64_t acols = transA ? m : k;
     for (int c = 0; c < pl.nparts; ++c) {
         const int64_t k0 = pl.kb[c], kp = pl.kb[c + 1] - pl.kb[c];
@@ -1007,8 +1052,9 @@ int cmm_multiply_host(const void *A, int64_t lda, int32_t transA, const void *B,
         e = cudaEventRecord(ev_in[c], cs);
         if (e != cudaSuccess) return cuda_fail(e, "operand part event");
     }
+    // the same split as the copies above (run_sketch plans with the same arguments)
     rc = run_sketch(dA, acols > 0 ? acols : 1, transA, dB, p > 0 ? p : 1, dtype, m, k, p, hs,
-                    prec, Rw, scratch, s, pl.nparts, ev_in);
+                    prec, Rw, scratch, s, pl.nparts, ev_in, ratio);
     if (rc) return rc;
     // the estimate in row blocks, each copied back while the next is extracted
     if (m > 0 && p > 0) {

@@ -28,8 +28,9 @@ def _pm1(shape, seed):
 @pytest.mark.parametrize("transA", [False, True])
 @pytest.mark.parametrize("n,prec", [(2048, "f32"), (2048, "f64"), (4096, "f32")])
 def test_host_path_split_matches_device_path(cmm, transA, n, prec):
-    # FP64 operands of 64 MiB or more: two parts along the inner index;
-    # estimates of 32 MiB or more: four row blocks
+    # FP64 operands of 64 MiB or more: two parts along the inner index (three
+    # from 256 MiB, n = 4096), growing geometrically; one row block per 16 MiB
+    # of the estimate (2 at n = 2048, 8 at n = 4096)
     A = _pm1((n, n), 1)
     A[5] = A[9]            # a planted pair: C[5, 9] = n
     B = A.T.copy()
