@@ -373,6 +373,16 @@ def run_cmm(a):
                           "max_abs_R_diff_vs_fp32": dR,
                           "equal_error": dR == 0.0}
 
+    # the heavy-hitter list straight from the sketch, without writing C
+    # (cmm_heavy_hitters on the step's R): same list as the step's
+    if world == 1:
+        hfn = lambda: cmm.heavy_hitters(R, h, n, n, tau, capacity=cap)
+        I2, J2, V2 = hfn()
+        same = bool(torch.equal(I2.cpu(), I.cpu()) and torch.equal(J2.cpu(), J.cpu())
+                    and torch.equal(V2.cpu(), V.cpu()))
+        result["heavy_hitters_from_R"] = {"ms": round(_events_ms(hfn, 5), 3),
+                                          "same_list_as_step": same}
+
     # cuBLAS DGEMM of the same product on the same GPU (the exact C): time of
     # one call after one warm-up, and the heavy hitters against the exact C
     if not a.no_dgemm and world == 1:

@@ -166,30 +166,40 @@ cudaError_t launch_hash_tables(const HashParams &hp, int d, int L, int64_t m, in
                                uint32_t *H1, uint32_t *H2, cudaStream_t s);
 // rows [0, m) of C; H1 holds each repetition's row hashes at stride ldh (pass
 // H1 + i0 and the full row count to extract rows i0 .. i0 + m - 1); cyclic
-// selects the bucket (h1 + h2) mod b of Sec. 3.1 instead of h1 XOR h2
-// With tcounts non-null the kernel also writes, per row i and tile of
-// hh_tiles columns, the number of its estimates inside the heavy-hitter range
+// selects the bucket (h1 + h2) mod b of Sec. 3.1 instead of h1 XOR h2.  With
+// tcounts non-null the kernel also writes, per row i and tile of 256 columns
+// (tile = j / 256), the number of its estimates inside the heavy-hitter range
 // hr to tcounts[i * ldt + tile], so that the list can be written without a
 // counting pass over C.
+int64_t hh_tiles(int64_t p);   // tiles per row: ceil(p / 256)
 cudaError_t launch_extract(const double *R, const uint32_t *H1, const uint32_t *H2, int d,
                            int L, int64_t m, int64_t p, int reduce, double *C, int64_t ldc,
                            int64_t ldh, cudaStream_t s, int cyclic = 0, HhRange hr = {1, 0},
                            int32_t *tcounts = nullptr, int64_t ldt = 0);
-// heavy hitters from R (estimates recomputed; C not written): hits per row,
-// then the ordered list
-cudaError_t launch_hh_count(const double *R, const uint32_t *H1, const uint32_t *H2, int d,
-                            int L, int64_t m, int64_t p, int reduce, HhRange hr,
-                            int64_t *counts, cudaStream_t s);
-cudaError_t launch_hh_scan(int64_t *counts, int64_t ntiles, cudaStream_t s);
+// exclusive scan of counts[0, n) into counts[n, 2n] (counts[2n] = total)
+cudaError_t launch_hh_scan(int64_t *counts, int64_t n, cudaStream_t s);
+// heavy hitters from R, estimates recomputed, at the offsets of a scan of the
+// per-row counts (the second pass when the candidates of launch_hh_cand overflow)
 cudaError_t launch_hh_write(const double *R, const uint32_t *H1, const uint32_t *H2, int d,
                             int L, int64_t m, int64_t p, int reduce, HhRange hr,
                             const int64_t *offsets, int32_t *I, int32_t *J, double *V,
                             int64_t capacity, cudaStream_t s);
+// heavy hitters from R in one pass: the estimates' hits as candidates
+// (ordered within each (row, tile)) at a counter's offsets, their count and
+// first offset per (row, tile); then, after the row scan and the scan of the
+// row totals, the candidates copied into the ordered list
+cudaError_t launch_hh_cand(const double *R, const uint32_t *H1, const uint32_t *H2, int d, int L,
+                           int64_t m, int64_t p, int reduce, HhRange hr, int32_t *tcounts,
+                           int64_t *tsrc, int64_t ldt, unsigned long long *ncand, int64_t ccap,
+                           int32_t *CI, int32_t *CJ, double *CV, cudaStream_t s);
+cudaError_t launch_hh_cand_copy(const int32_t *tinc, const int64_t *tsrc, int64_t ldt, int64_t m,
+                                int64_t p, const int64_t *offsets, const int32_t *CI,
+                                const int32_t *CJ, const double *CV, int64_t ccap, int32_t *I,
+                                int32_t *J, double *V, int64_t capacity, cudaStream_t s);
 // heavy hitters of a dense m x p estimate C: hits per (row, tile) (the same
 // tiles as launch_extract's counts); per row, the tile counts turned in place
 // into their inclusive prefix and the row total into counts[i]; then the
 // ordered list, one warp per tile that holds hits
-int64_t hh_tiles(int64_t p);
 cudaError_t launch_hh_tile_count(const double *C, int64_t ldc, int64_t m, int64_t p, HhRange hr,
                                  int32_t *tcounts, int64_t ldt, cudaStream_t s);
 cudaError_t launch_hh_rowscan(int32_t *tcounts, int64_t ldt, int64_t m, int64_t p,

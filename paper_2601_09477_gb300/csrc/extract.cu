@@ -126,6 +126,141 @@ __global__ void __launch_bounds__(kThreads) extract_kernel(const double *__restr
     }
 }
 
+// Heavy hitters from R in one pass over the estimates (no C): the CTA of
+// extract_kernel's tile (kRowsPerBlock rows x kThreads columns) computes its
+// estimates, keeps the hits' values in shared memory, reserves room for them
+// with one atomic on a global candidate counter and writes them there in
+// (row, column) order; per (row, tile) it records the count and the offset of
+// its first candidate.  Candidates past `ccap` are dropped (the caller then
+// falls back to the two-pass count / write kernels).
+template <int D>
+__global__ void __launch_bounds__(kThreads) hh_cand_kernel(
+    const double *__restrict__ R, const uint32_t *__restrict__ H1, const uint32_t *__restrict__ H2,
+    int d, int L, int64_t m, int64_t p, int reduce, HhRange hr, int32_t *__restrict__ tcounts,
+    int64_t *__restrict__ tsrc, int64_t ldt, unsigned long long *__restrict__ ncand, int64_t ccap,
+    int32_t *__restrict__ CI, int32_t *__restrict__ CJ, double *__restrict__ CV) {
+    __shared__ uint32_t h1s[kRowsPerBlock][CMM_MAX_D];
+    __shared__ int s_cnt[kRowsPerBlock][kThreads / 32];   // hits per (row, warp), then its prefix
+    __shared__ int s_row[kRowsPerBlock + 1];               // exclusive prefix over the rows, total
+    __shared__ long long s_base;
+    __shared__ double s_val[kRowsPerBlock][kThreads];
+    const int64_t b = (int64_t)1 << L;
+    const uint32_t mask = (uint32_t)(b - 1);
+    const int64_t col_tiles = (p + kThreads - 1) / kThreads;
+    const int64_t tile = blockIdx.x % col_tiles;
+    const int64_t i0 = (blockIdx.x / col_tiles) * kRowsPerBlock;
+    const int64_t j = tile * kThreads + threadIdx.x;
+    const int dd = D > 0 ? D : d;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int e = threadIdx.x; e < kRowsPerBlock * dd; e += kThreads) {
+        const int rr = e / dd, r = e % dd;
+        h1s[rr][r] = (i0 + rr < m) ? H1[(int64_t)r * m + i0 + rr] : 0u;
+    }
+    __syncthreads();
+    uint32_t hits = 0;
+    if (j < p) {
+        if constexpr (D > 0) {
+            uint32_t h2v[D];
+#pragma unroll
+            for (int r = 0; r < D; ++r) h2v[r] = H2[(int64_t)r * p + j];
+#pragma unroll 1
+            for (int rr = 0; rr < kRowsPerBlock && i0 + rr < m; ++rr) {
+                const double e = estimate_fixed<D>(R, b, mask, h1s[rr], h2v, reduce);
+                if (hh_hit(e, hr)) {
+                    s_val[rr][threadIdx.x] = e;
+                    hits |= 1u << rr;
+                }
+            }
+        } else {
+            long long v[CMM_MAX_D];
+            for (int rr = 0; rr < kRowsPerBlock && i0 + rr < m; ++rr) {
+                for (int r = 0; r < d; ++r)
+                    v[r] = rep_key(R + r * b, h1s[rr][r], H2[(int64_t)r * p + j], mask);
+                const double e = combine_generic(v, d, reduce);
+                if (hh_hit(e, hr)) {
+                    s_val[rr][threadIdx.x] = e;
+                    hits |= 1u << rr;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int rr = 0; rr < kRowsPerBlock; ++rr) {
+        const unsigned bal = __ballot_sync(0xffffffffu, (hits >> rr) & 1u);
+        if (lane == 0) s_cnt[rr][warp] = __popc(bal);
+    }
+    __syncthreads();
+    if (threadIdx.x < kRowsPerBlock) {   // one thread per row: warp prefix, row total
+        const int rr = threadIdx.x;
+        int run = 0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) {
+            const int c = s_cnt[rr][w];
+            s_cnt[rr][w] = run;
+            run += c;
+        }
+        s_row[rr] = run;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int rr = 0; rr < kRowsPerBlock; ++rr) {
+            const int c = s_row[rr];
+            s_row[rr] = run;
+            run += c;
+        }
+        s_row[kRowsPerBlock] = run;
+        s_base = run ? (long long)atomicAdd(ncand, (unsigned long long)run) : 0;
+    }
+    __syncthreads();
+    const long long base = s_base;
+#pragma unroll
+    for (int rr = 0; rr < kRowsPerBlock; ++rr) {
+        const bool hit = (hits >> rr) & 1u;
+        const unsigned bal = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+            const long long pos = base + s_row[rr] + s_cnt[rr][warp] + __popc(bal & ((1u << lane) - 1u));
+            if (pos < ccap) {
+                CI[pos] = (int32_t)(i0 + rr);
+                CJ[pos] = (int32_t)j;
+                CV[pos] = s_val[rr][threadIdx.x];
+            }
+        }
+    }
+    if (threadIdx.x < kRowsPerBlock && i0 + threadIdx.x < m) {
+        const int rr = threadIdx.x;
+        tcounts[(i0 + rr) * ldt + tile] = s_row[rr + 1] - s_row[rr];
+        tsrc[(i0 + rr) * ldt + tile] = base + s_row[rr];
+    }
+}
+
+// after hh_rowscan_kernel (inclusive prefix of the tile counts per row, row
+// totals) and the scan of the row totals: each (row, tile)'s candidates are
+// copied to their place in the ordered list, one warp per (row, tile)
+__global__ void __launch_bounds__(kThreads) hh_cand_copy_kernel(
+    const int32_t *__restrict__ tinc, const int64_t *__restrict__ tsrc, int64_t ldt, int64_t m,
+    int64_t nt, const int64_t *__restrict__ offsets, const int32_t *__restrict__ CI,
+    const int32_t *__restrict__ CJ, const double *__restrict__ CV, int64_t ccap,
+    int32_t *__restrict__ I, int32_t *__restrict__ J, double *__restrict__ V, int64_t capacity) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t item = w0; item < m * nt; item += nw) {
+        const int64_t i = item / nt, t = item % nt;
+        const int hi = tinc[i * ldt + t];
+        const int lo = t > 0 ? tinc[i * ldt + t - 1] : 0;
+        if (hi == lo) continue;
+        const int64_t dst = offsets[i] + lo, src = tsrc[i * ldt + t];
+        for (int e = lane; e < hi - lo; e += 32) {
+            if (dst + e < capacity && src + e < ccap) {   // past ccap: the second pass writes it
+                I[dst + e] = CI[src + e];
+                J[dst + e] = CJ[src + e];
+                V[dst + e] = CV[src + e];
+            }
+        }
+    }
+}
+
 // estimate of (i, j) for the heavy-hitter passes (row words in shared memory)
 template <int D>
 __device__ __forceinline__ double estimate_at(const double *__restrict__ R, int64_t b, uint32_t mask,
@@ -140,33 +275,6 @@ __device__ __forceinline__ double estimate_at(const double *__restrict__ R, int6
         long long v[CMM_MAX_D];
         for (int r = 0; r < d; ++r) v[r] = rep_key(R + r * b, h1s[r], H2[(int64_t)r * p + j], mask);
         return combine_generic(v, d, reduce);
-    }
-}
-
-// heavy hitters from R, pass 1: hits per row
-template <int D>
-__global__ void __launch_bounds__(kThreads) hh_count_kernel(
-    const double *__restrict__ R, const uint32_t *__restrict__ H1, const uint32_t *__restrict__ H2,
-    int d, int L, int64_t m, int64_t p, int reduce, HhRange hr, int64_t *__restrict__ counts) {
-    __shared__ uint32_t h1s[CMM_MAX_D];
-    __shared__ int64_t wsum[kThreads / 32];
-    const int64_t b = (int64_t)1 << L;
-    const uint32_t mask = (uint32_t)(b - 1);
-    for (int64_t i = blockIdx.x; i < m; i += gridDim.x) {
-        for (int r = threadIdx.x; r < d; r += kThreads) h1s[r] = H1[(int64_t)r * m + i];
-        __syncthreads();
-        int64_t cnt = 0;
-        for (int64_t j = threadIdx.x; j < p; j += kThreads)
-            cnt += hh_hit(estimate_at<D>(R, b, mask, h1s, H2, p, j, d, reduce), hr);
-        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int64_t s = 0;
-            for (int w = 0; w < kThreads / 32; ++w) s += wsum[w];
-            counts[i] = s;
-        }
-        __syncthreads();
     }
 }
 
@@ -208,7 +316,8 @@ __global__ void __launch_bounds__(1024) hh_scan_kernel(const int64_t *__restrict
     if (q == 1023) offsets[n] = run;
 }
 
-// heavy hitters from R, pass 2: ordered compaction of each row's hits
+// heavy hitters from R, second pass (when the candidates overflowed): the
+// ordered compaction of each row's hits, estimates recomputed
 template <int D>
 __global__ void __launch_bounds__(kThreads) hh_write_kernel(
     const double *__restrict__ R, const uint32_t *__restrict__ H1, const uint32_t *__restrict__ H2,
@@ -444,19 +553,6 @@ cudaError_t launch_extract(const double *R, const uint32_t *H1, const uint32_t *
                                             ldt, s);
 }
 
-cudaError_t launch_hh_count(const double *R, const uint32_t *H1, const uint32_t *H2, int d, int L,
-                            int64_t m, int64_t p, int reduce, HhRange hr, int64_t *counts,
-                            cudaStream_t s) {
-    const unsigned g = clamp_grid(m);
-    switch (d) {
-#define X(D) case D: hh_count_kernel<D><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, hr, counts); break;
-        CMM_ODD_D_CASES(X)
-#undef X
-        default: hh_count_kernel<0><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, hr, counts);
-    }
-    return cudaGetLastError();
-}
-
 int64_t hh_tiles(int64_t p) { return (p + kHhTile - 1) / kHhTile; }
 
 cudaError_t launch_hh_tile_count(const double *C, int64_t ldc, int64_t m, int64_t p, HhRange hr,
@@ -482,6 +578,33 @@ cudaError_t launch_hh_tile_write(const double *C, int64_t ldc, int64_t m, int64_
     const unsigned g = clamp_grid((items + kThreads / 32 - 1) / (kThreads / 32));
     hh_tile_write_kernel<<<g, kThreads, 0, s>>>(C, ldc, m, p, hr, tinc, ldt, offsets, I, J, V,
                                                 capacity);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hh_cand(const double *R, const uint32_t *H1, const uint32_t *H2, int d, int L,
+                           int64_t m, int64_t p, int reduce, HhRange hr, int32_t *tcounts,
+                           int64_t *tsrc, int64_t ldt, unsigned long long *ncand, int64_t ccap,
+                           int32_t *CI, int32_t *CJ, double *CV, cudaStream_t s) {
+    const int64_t blocks = ((m + kRowsPerBlock - 1) / kRowsPerBlock) * ((p + kThreads - 1) / kThreads);
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const unsigned g = (unsigned)blocks;
+    switch (d) {
+#define X(D) case D: hh_cand_kernel<D><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, hr, tcounts, tsrc, ldt, ncand, ccap, CI, CJ, CV); break;
+        CMM_ODD_D_CASES(X)
+#undef X
+        default: hh_cand_kernel<0><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, hr, tcounts, tsrc, ldt, ncand, ccap, CI, CJ, CV);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hh_cand_copy(const int32_t *tinc, const int64_t *tsrc, int64_t ldt, int64_t m,
+                                int64_t p, const int64_t *offsets, const int32_t *CI,
+                                const int32_t *CJ, const double *CV, int64_t ccap, int32_t *I,
+                                int32_t *J, double *V, int64_t capacity, cudaStream_t s) {
+    const int64_t items = m * hh_tiles(p);
+    const unsigned g = clamp_grid((items + kThreads / 32 - 1) / (kThreads / 32));
+    hh_cand_copy_kernel<<<g, kThreads, 0, s>>>(tinc, tsrc, ldt, m, hh_tiles(p), offsets, CI, CJ,
+                                               CV, ccap, I, J, V, capacity);
     return cudaGetLastError();
 }
 

@@ -255,24 +255,43 @@ int check_operands(const void *A, int64_t lda, int transA, const void *B, int64_
     return CMM_OK;
 }
 
+// candidates of the one-pass heavy-hitter list from R: one per 64 entries of
+// the estimate, within [2^16, 2^24] (more hits fall back to a second pass)
+int64_t hh_cand_capacity(int64_t m, int64_t p) {
+    const double e = (double)m * (double)p / 64.0;
+    return (int64_t)std::min(16777216.0, std::max(65536.0, e));
+}
+
 // extraction workspace: hash words of rows and columns, per-row counts and
-// offsets (2m + 1), per-(row, tile) counts of the dense heavy-hitter passes
+// offsets (2m + 1), per-(row, tile) counts and candidate offsets of the
+// heavy-hitter passes, the candidate counter and the candidates (i, j, value)
 size_t extract_ws_bytes(int64_t m, int64_t p, int d) {
+    const size_t mt = (size_t)m * hh_tiles(p);
+    const size_t cc = (size_t)hh_cand_capacity(m, p);
     return align_up((size_t)d * m * 4) + align_up((size_t)d * p * 4) +
-           align_up((size_t)(2 * m + 1) * sizeof(int64_t)) +
-           align_up((size_t)m * hh_tiles(p) * sizeof(int32_t));
+           align_up((size_t)(2 * m + 1) * sizeof(int64_t)) + align_up(mt * sizeof(int32_t)) +
+           align_up(mt * sizeof(int64_t)) + align_up(sizeof(unsigned long long)) +
+           2 * align_up(cc * sizeof(int32_t)) + align_up(cc * sizeof(double));
 }
 
 struct ExtractWs {
     uint32_t *H1, *H2;
     int64_t *counts;
     int32_t *tcounts;   // m x nt, row stride nt
+    int64_t *tsrc;      // m x nt: offset of a (row, tile)'s first candidate
     int64_t nt;
+    unsigned long long *ncand;
+    int64_t ccap;
+    int32_t *CI, *CJ;
+    double *CV;
 };
 
 ExtractWs carve_extract(void *ws, int64_t m, int64_t p, int d) {
     char *base = static_cast<char *>(ws);
     ExtractWs e;
+    e.nt = hh_tiles(p);
+    e.ccap = hh_cand_capacity(m, p);
+    const size_t mt = (size_t)m * e.nt;
     e.H1 = reinterpret_cast<uint32_t *>(base);
     base += align_up((size_t)d * m * 4);
     e.H2 = reinterpret_cast<uint32_t *>(base);
@@ -280,7 +299,16 @@ ExtractWs carve_extract(void *ws, int64_t m, int64_t p, int d) {
     e.counts = reinterpret_cast<int64_t *>(base);
     base += align_up((size_t)(2 * m + 1) * sizeof(int64_t));
     e.tcounts = reinterpret_cast<int32_t *>(base);
-    e.nt = hh_tiles(p);
+    base += align_up(mt * sizeof(int32_t));
+    e.tsrc = reinterpret_cast<int64_t *>(base);
+    base += align_up(mt * sizeof(int64_t));
+    e.ncand = reinterpret_cast<unsigned long long *>(base);
+    base += align_up(sizeof(unsigned long long));
+    e.CI = reinterpret_cast<int32_t *>(base);
+    base += align_up((size_t)e.ccap * sizeof(int32_t));
+    e.CJ = reinterpret_cast<int32_t *>(base);
+    base += align_up((size_t)e.ccap * sizeof(int32_t));
+    e.CV = reinterpret_cast<double *>(base);
     return e;
 }
 
@@ -410,26 +438,25 @@ int run_extract(const double *R, const cmm_hashes *hs, int64_t m, int64_t p, int
     return CMM_OK;
 }
 
-// The heavy-hitter list, given per-(row, tile) counts in ew.tcounts (dense C)
-// or per-row counts in ew.counts (from R): row sums, a scan into offsets, each
-// row's hits written in column order (rows past `capacity` are skipped on the
-// device), then the total is read.  One host synchronisation, at the end.
-int finish_hh(const double *R, const ExtractWs &ew, const double *C, int64_t ldc, int64_t m,
-              int64_t p, int d, int L, int reduce, HhRange hr, int32_t *I, int32_t *J, double *V,
-              int64_t capacity, int64_t *count, cudaStream_t s) {
+// The heavy-hitter list of a dense C, given per-(row, tile) counts in
+// ew.tcounts: row totals (and per row the tiles' inclusive prefix), a scan
+// into offsets, each row's hits written in column order by the tiles that
+// hold them (rows past `capacity` are skipped on the device), then the total
+// is read.  One host synchronisation, at the end.
+int finish_hh(const ExtractWs &ew, const double *C, int64_t ldc, int64_t m, int64_t p,
+              HhRange hr, int32_t *I, int32_t *J, double *V, int64_t capacity, int64_t *count,
+              cudaStream_t s) {
     cudaError_t e;
     {
-        Span sp("hh_scan", s, C ? 2 : 1);
-        e = C ? launch_hh_rowscan(ew.tcounts, ew.nt, m, p, ew.counts, s) : cudaSuccess;
+        Span sp("hh_scan", s, 2);
+        e = launch_hh_rowscan(ew.tcounts, ew.nt, m, p, ew.counts, s);
         if (e == cudaSuccess) e = launch_hh_scan(ew.counts, m, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter scan");
     if (capacity > 0) {
-        Span sp(C ? "hh_write_dense" : "hh_write", s);
-        e = C ? launch_hh_tile_write(C, ldc, m, p, hr, ew.tcounts, ew.nt, ew.counts + m, I, J, V,
-                                     capacity, s)
-              : launch_hh_write(R, ew.H1, ew.H2, d, L, m, p, reduce, hr, ew.counts + m, I, J, V,
-                                capacity, s);
+        Span sp("hh_write_dense", s);
+        e = launch_hh_tile_write(C, ldc, m, p, hr, ew.tcounts, ew.nt, ew.counts + m, I, J, V,
+                                 capacity, s);
         if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter write");
     }
     int64_t total = 0;
@@ -444,31 +471,84 @@ int finish_hh(const double *R, const ExtractWs &ew, const double *C, int64_t ldc
     return CMM_OK;
 }
 
-// heavy hitters of the dense C (hs null) or of the estimates from R
-int run_hh(const double *R, const cmm_hashes *hs, const double *C, int64_t ldc, int64_t m,
-           int64_t p, int d, int L, int reduce, double tau, int32_t *I, int32_t *J, double *V,
-           int64_t capacity, int64_t *count, void *ws, cudaStream_t s) {
+// heavy hitters of the dense C
+int run_hh_dense(const double *C, int64_t ldc, int64_t m, int64_t p, double tau, int32_t *I,
+                 int32_t *J, double *V, int64_t capacity, int64_t *count, void *ws,
+                 cudaStream_t s) {
     *count = 0;
     if (m == 0 || p == 0) return CMM_OK;
-    ExtractWs ew = carve_extract(ws, m, p, d);
+    ExtractWs ew = carve_extract(ws, m, p, 1);
     const HhRange hr = hh_range(tau);
     cudaError_t e;
-    if (C) {
+    {
         Span sp("hh_count_dense", s);
         e = launch_hh_tile_count(C, ldc, m, p, hr, ew.tcounts, ew.nt, s);
-    } else {
-        HashParams hp;
-        fill_params(hs, hp);
-        {
-            Span sp("hash_tables", s);
-            e = launch_hash_tables(hp, d, L, m, p, ew.H1, ew.H2, s);
-        }
-        if (e != cudaSuccess) return cuda_fail(e, "hash tables");
-        Span sp("hh_count", s);
-        e = launch_hh_count(R, ew.H1, ew.H2, d, L, m, p, reduce, hr, ew.counts, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter count");
-    return finish_hh(R, ew, C, ldc, m, p, d, L, reduce, hr, I, J, V, capacity, count, s);
+    return finish_hh(ew, C, ldc, m, p, hr, I, J, V, capacity, count, s);
+}
+
+// heavy hitters of the estimates from R, without writing C: one pass over the
+// estimates writes the hits as candidates and counts them per (row, tile);
+// row scan, scan, and the candidates are copied into order.  If there were
+// more hits than candidate room, the list is written by a second pass that
+// recomputes the estimates (the counts and offsets of the first stay valid).
+int run_hh_R(const double *R, const cmm_hashes *hs, int64_t m, int64_t p, int reduce,
+             double tau, int32_t *I, int32_t *J, double *V, int64_t capacity, int64_t *count,
+             void *ws, cudaStream_t s) {
+    *count = 0;
+    if (m == 0 || p == 0) return CMM_OK;
+    const int d = hs->d, L = hs->log2b;
+    ExtractWs ew = carve_extract(ws, m, p, d);
+    const HhRange hr = hh_range(tau);
+    HashParams hp;
+    fill_params(hs, hp);
+    cudaError_t e;
+    {
+        Span sp("hash_tables", s);
+        e = launch_hash_tables(hp, d, L, m, p, ew.H1, ew.H2, s);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(ew.ncand, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "hash tables");
+    {
+        Span sp("hh_candidates", s);
+        e = launch_hh_cand(R, ew.H1, ew.H2, d, L, m, p, reduce, hr, ew.tcounts, ew.tsrc, ew.nt,
+                           ew.ncand, ew.ccap, ew.CI, ew.CJ, ew.CV, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter candidates");
+    {
+        Span sp("hh_scan", s, 2);
+        e = launch_hh_rowscan(ew.tcounts, ew.nt, m, p, ew.counts, s);
+        if (e == cudaSuccess) e = launch_hh_scan(ew.counts, m, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter scan");
+    if (capacity > 0) {
+        Span sp("hh_copy", s);
+        e = launch_hh_cand_copy(ew.tcounts, ew.tsrc, ew.nt, m, p, ew.counts + m, ew.CI, ew.CJ,
+                                ew.CV, ew.ccap, I, J, V, capacity, s);
+        if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter copy");
+    }
+    int64_t total = 0;
+    unsigned long long ncand = 0;
+    e = cudaMemcpyAsync(&total, ew.counts + 2 * m, sizeof total, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&ncand, ew.ncand, sizeof ncand, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter sync");
+    if ((int64_t)ncand > ew.ccap && capacity > 0) {
+        {
+            Span sp("hh_write", s);
+            e = launch_hh_write(R, ew.H1, ew.H2, d, L, m, p, reduce, hr, ew.counts + m, I, J, V,
+                                capacity, s);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter write");
+    }
+    *count = total;
+    if (total > capacity)
+        return fail(CMM_ERR_CAPACITY, "%lld heavy hitters, capacity %lld", (long long)total,
+                    (long long)capacity);
+    return CMM_OK;
 }
 
 // ---- adjoint planning --------------------------------------------------------
@@ -779,8 +859,8 @@ int cmm_heavy_hitters(const double *R, const cmm_hashes *hs, int64_t m, int64_t 
     if (capacity > 0 && (!I || !J || !V)) return fail(CMM_ERR_ARG, "I, J or V is NULL");
     rc = check_ws(ws, ws_bytes, extract_ws_bytes(m, p, hs->d));
     if (rc) return rc;
-    return run_hh(R, hs, nullptr, 0, m, p, hs->d, hs->log2b, reduce, tau, I, J, V, capacity, count,
-                  ws, static_cast<cudaStream_t>(stream));
+    return run_hh_R(R, hs, m, p, reduce, tau, I, J, V, capacity, count, ws,
+                    static_cast<cudaStream_t>(stream));
 }
 
 int cmm_threshold(const double *C, int64_t m, int64_t p, int64_t ldc, double tau, int32_t *I,
@@ -795,8 +875,8 @@ int cmm_threshold(const double *C, int64_t m, int64_t p, int64_t ldc, double tau
     if (capacity > 0 && (!I || !J || !V)) return fail(CMM_ERR_ARG, "I, J or V is NULL");
     rc = check_ws(ws, ws_bytes, extract_ws_bytes(m, p, 1));
     if (rc) return rc;
-    return run_hh(nullptr, nullptr, C, ldc, m, p, 1, 1, CMM_MEDIAN, tau, I, J, V, capacity, count,
-                  ws, static_cast<cudaStream_t>(stream));
+    return run_hh_dense(C, ldc, m, p, tau, I, J, V, capacity, count, ws,
+                        static_cast<cudaStream_t>(stream));
 }
 
 size_t cmm_multiply_workspace_bytes(int64_t m, int64_t k, int64_t p, int32_t d, int32_t log2b,
@@ -865,8 +945,8 @@ int cmm_multiply_threshold(const void *A, int64_t lda, int32_t transA, const voi
     const HhRange hr = hh_range(tau);
     rc = run_extract(Rw, hs, m, p, reduce, C, ldc, scratch, s, 0, &hr);
     if (rc) return rc;
-    return finish_hh(nullptr, carve_extract(scratch, m, p, hs->d), C, ldc, m, p, hs->d,
-                     hs->log2b, reduce, hr, I, J, V, capacity, count, s);
+    return finish_hh(carve_extract(scratch, m, p, hs->d), C, ldc, m, p, hr, I, J, V, capacity,
+                     count, s);
 }
 
 namespace {
@@ -1091,8 +1171,8 @@ int cmm_multiply_host(const void *A, int64_t lda, int32_t transA, const void *B,
     }
     int hh_rc = CMM_OK;
     if (count && m > 0 && p > 0) {
-        hh_rc = finish_hh(nullptr, carve_extract(scratch, m, p, hs->d), dC, p, m, p, hs->d,
-                          hs->log2b, reduce, hr, dI, dJ, dV, cap, count, s);
+        hh_rc = finish_hh(carve_extract(scratch, m, p, hs->d), dC, p, m, p, hr, dI, dJ, dV, cap,
+                          count, s);
         if (hh_rc != CMM_OK && hh_rc != CMM_ERR_CAPACITY) return hh_rc;
         const int64_t n = std::min(*count, cap);
         if (n > 0) {

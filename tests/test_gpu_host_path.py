@@ -49,6 +49,25 @@ def test_host_path_split_matches_device_path(cmm, transA, n, prec):
     assert (5, 9) in set(zip(I.tolist(), J.tolist()))
 
 
+def test_host_path_four_parts_full_size(cmm):
+    # the benchmark's size: 1 GiB of FP64 operands in four parts, 512 MiB of
+    # estimate in eight row blocks; bit-identical to the device path on +-1
+    n = 8192
+    A = _pm1((n, n), 7)
+    A[11] = A[3]
+    Ah = torch.from_numpy(A).pin_memory()
+    Bh = torch.from_numpy(np.ascontiguousarray(A.T)).pin_memory()
+    h = cmm.make_hashes(2002, 9, 16)
+    Ch, (I, J, V) = cmm.multiply_host(Ah, Bh, h, prec="f32", tau=n / 2, capacity=1 << 22)
+    Ad, Bd = Ah.cuda(), Bh.cuda()
+    Cd, (Id, Jd, Vd) = cmm.multiply_threshold(Ad, Bd, h, n / 2, capacity=1 << 22, prec="f32")
+    assert torch.equal(Ch, Cd.cpu())
+    assert np.array_equal(I.numpy(), Id.cpu().numpy())
+    assert np.array_equal(J.numpy(), Jd.cpu().numpy())
+    assert np.array_equal(V.numpy(), Vd.cpu().numpy())
+    assert (3, 11) in set(zip(I.tolist(), J.tolist()))
+
+
 def test_host_path_padded_small(cmm):
     # below the split thresholds: one part, one row block; padded leading
     # dimensions on the host side

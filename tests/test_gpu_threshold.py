@@ -118,3 +118,23 @@ def test_multiply_threshold_empty(cmm):
     B = torch.ones((5, 9), dtype=torch.float64, device="cuda")
     C, (I, J, V) = cmm.multiply_threshold(A, B, h, 0.0, capacity=4)
     assert C.shape == (0, 9) and I.numel() == 0
+
+
+@pytest.mark.parametrize("m,p,L,d,tau", [
+    (700, 1500, 11, 5, 1.0),     # candidates fit: one pass over the estimates
+    (512, 600, 10, 5, 0.0),      # every entry a hit: 307,200 > 65,536 candidates, second pass
+    (33, 4099, 9, 4, 1.5),       # ragged tiles, even d
+])
+def test_heavy_hitters_from_R_one_pass(cmm, m, p, L, d, tau):
+    g = np.random.default_rng(m + p)
+    R = g.standard_normal((d, 1 << L)) * 2
+    h = cmm.make_hashes(50 + L, d, L)
+    I, J, V = cmm.heavy_hitters(_dev(R), h, m, p, tau=tau, capacity=m * p)
+    Io, Jo, Vo = orc.heavy_hitters(R, h.params, m, p, tau, capacity=m * p)
+    assert np.array_equal(I.cpu().numpy(), Io)
+    assert np.array_equal(J.cpu().numpy(), Jo)
+    assert np.array_equal(V.cpu().numpy(), Vo)
+    # and the same list as Decompress + threshold
+    C = cmm.extract(_dev(R), h, m, p)
+    I2, J2, V2 = cmm.threshold(C, tau, capacity=m * p)
+    assert torch.equal(I, I2) and torch.equal(J, J2) and torch.equal(V, V2)
