@@ -166,16 +166,11 @@ cudaError_t launch_hash_tables(const HashParams &hp, int d, int L, int64_t m, in
                                uint32_t *H1, uint32_t *H2, cudaStream_t s);
 // rows [0, m) of C; H1 holds each repetition's row hashes at stride ldh (pass
 // H1 + i0 and the full row count to extract rows i0 .. i0 + m - 1); cyclic
-// selects the bucket (h1 + h2) mod b of Sec. 3.1 instead of h1 XOR h2.  With
-// tcounts non-null the kernel also writes, per row i and tile of 256 columns
-// (tile = j / 256), the number of its estimates inside the heavy-hitter range
-// hr to tcounts[i * ldt + tile], so that the list can be written without a
-// counting pass over C.
-int64_t hh_tiles(int64_t p);   // tiles per row: ceil(p / 256)
+// selects the bucket (h1 + h2) mod b of Sec. 3.1 instead of h1 XOR h2
 cudaError_t launch_extract(const double *R, const uint32_t *H1, const uint32_t *H2, int d,
                            int L, int64_t m, int64_t p, int reduce, double *C, int64_t ldc,
-                           int64_t ldh, cudaStream_t s, int cyclic = 0, HhRange hr = {1, 0},
-                           int32_t *tcounts = nullptr, int64_t ldt = 0);
+                           int64_t ldh, cudaStream_t s, int cyclic = 0);
+int64_t hh_tiles(int64_t p);   // tiles of 256 columns per row: ceil(p / 256)
 // exclusive scan of counts[0, n) into counts[n, 2n] (counts[2n] = total)
 cudaError_t launch_hh_scan(int64_t *counts, int64_t n, cudaStream_t s);
 // heavy hitters from R, estimates recomputed, at the offsets of a scan of the
@@ -184,20 +179,24 @@ cudaError_t launch_hh_write(const double *R, const uint32_t *H1, const uint32_t 
                             int L, int64_t m, int64_t p, int reduce, HhRange hr,
                             const int64_t *offsets, int32_t *I, int32_t *J, double *V,
                             int64_t capacity, cudaStream_t s);
-// heavy hitters from R in one pass: the estimates' hits as candidates
-// (ordered within each (row, tile)) at a counter's offsets, their count and
-// first offset per (row, tile); then, after the row scan and the scan of the
-// row totals, the candidates copied into the ordered list
+// heavy hitters in one pass over the estimates of rows [0, m) (H1 at stride
+// ldh as in launch_extract; row0 = the first row's index in the whole C):
+// with C non-null the estimates are also written to C; the hits become
+// candidates (ordered within each (row, tile of 256 columns)) at offsets of a
+// counter, with their count and first offset per (row, tile); then, after
+// the row scan and the scan of the row totals, the candidates are copied into
+// the ordered list
 cudaError_t launch_hh_cand(const double *R, const uint32_t *H1, const uint32_t *H2, int d, int L,
-                           int64_t m, int64_t p, int reduce, HhRange hr, int32_t *tcounts,
-                           int64_t *tsrc, int64_t ldt, unsigned long long *ncand, int64_t ccap,
-                           int32_t *CI, int32_t *CJ, double *CV, cudaStream_t s);
+                           int64_t m, int64_t p, int64_t ldh, int64_t row0, int reduce, HhRange hr,
+                           double *C, int64_t ldc, int32_t *tcounts, int64_t *tsrc, int64_t ldt,
+                           unsigned long long *ncand, int64_t ccap, int32_t *CI, int32_t *CJ,
+                           double *CV, cudaStream_t s);
 cudaError_t launch_hh_cand_copy(const int32_t *tinc, const int64_t *tsrc, int64_t ldt, int64_t m,
                                 int64_t p, const int64_t *offsets, const int32_t *CI,
                                 const int32_t *CJ, const double *CV, int64_t ccap, int32_t *I,
                                 int32_t *J, double *V, int64_t capacity, cudaStream_t s);
-// heavy hitters of a dense m x p estimate C: hits per (row, tile) (the same
-// tiles as launch_extract's counts); per row, the tile counts turned in place
+// heavy hitters of a dense m x p estimate C: hits per (row, tile) (the
+// tiles of launch_hh_cand); per row, the tile counts turned in place
 // into their inclusive prefix and the row total into counts[i]; then the
 // ordered list, one warp per tile that holds hits
 cudaError_t launch_hh_tile_count(const double *C, int64_t ldc, int64_t m, int64_t p, HhRange hr,

@@ -57,86 +57,57 @@ __global__ void hash_tables_kernel(const __grid_constant__ HashParams hp, int d,
 }
 
 // dense estimate: a CTA covers kRowsPerBlock rows x kThreads columns; each
-// thread keeps its column's d hash words in registers.  With CNT the CTA also
-// writes, for each of its rows, the number of its estimates that pass the
-// heavy-hitter test: tcounts[i * ldt + column tile] (one bit per row and
-// thread during the row loop, counted after it).
-template <int D, bool CYC, bool CNT>
+// thread keeps its column's d hash words in registers
+template <int D, bool CYC>
 __global__ void __launch_bounds__(kThreads) extract_kernel(const double *__restrict__ R,
                                                            const uint32_t *__restrict__ H1,
                                                            const uint32_t *__restrict__ H2, int d,
                                                            int L, int64_t m, int64_t p, int reduce,
                                                            double *__restrict__ C, int64_t ldc,
-                                                           int64_t ldh, HhRange hr,
-                                                           int32_t *__restrict__ tcounts,
-                                                           int64_t ldt) {
+                                                           int64_t ldh) {
     __shared__ uint32_t h1s[kRowsPerBlock][CMM_MAX_D];
-    __shared__ int s_cnt[kRowsPerBlock][kThreads / 32];
     const int64_t b = (int64_t)1 << L;
     const uint32_t mask = (uint32_t)(b - 1);
     const int64_t col_tiles = (p + kThreads - 1) / kThreads;
-    const int64_t tile = blockIdx.x % col_tiles;
     const int64_t i0 = (blockIdx.x / col_tiles) * kRowsPerBlock;
-    const int64_t j = tile * kThreads + threadIdx.x;
+    const int64_t j = (blockIdx.x % col_tiles) * kThreads + threadIdx.x;
     const int dd = D > 0 ? D : d;
     for (int e = threadIdx.x; e < kRowsPerBlock * dd; e += kThreads) {
         const int rr = e / dd, r = e % dd;
         h1s[rr][r] = (i0 + rr < m) ? H1[(int64_t)r * ldh + i0 + rr] : 0u;
     }
     __syncthreads();
-    uint32_t hits = 0;   // bit rr: row i0 + rr passes the heavy-hitter test here
-    if (j < p) {
-        if constexpr (D > 0) {
-            uint32_t h2v[D];
+    if (j >= p) return;
+    if constexpr (D > 0) {
+        uint32_t h2v[D];
 #pragma unroll
-            for (int r = 0; r < D; ++r) h2v[r] = H2[(int64_t)r * p + j];
-#pragma unroll 1
-            for (int rr = 0; rr < kRowsPerBlock && i0 + rr < m; ++rr) {
-                const double e = estimate_fixed<D, CYC>(R, b, mask, h1s[rr], h2v, reduce);
-                C[(i0 + rr) * ldc + j] = e;
-                if constexpr (CNT) hits |= (uint32_t)hh_hit(e, hr) << rr;
-            }
-        } else {
-            long long v[CMM_MAX_D];
-            for (int rr = 0; rr < kRowsPerBlock && i0 + rr < m; ++rr) {
-                for (int r = 0; r < d; ++r)
-                    v[r] = rep_key<CYC>(R + r * b, h1s[rr][r], H2[(int64_t)r * p + j], mask);
-                const double e = combine_generic(v, d, reduce);
-                C[(i0 + rr) * ldc + j] = e;
-                if constexpr (CNT) hits |= (uint32_t)hh_hit(e, hr) << rr;
-            }
-        }
-    }
-    if constexpr (CNT) {
-        // lanes past p (and rows past m) hold no bits
-        const int warp = threadIdx.x >> 5;
-#pragma unroll
-        for (int rr = 0; rr < kRowsPerBlock; ++rr) {
-            const unsigned bal = __ballot_sync(0xffffffffu, (hits >> rr) & 1u);
-            if ((threadIdx.x & 31) == 0) s_cnt[rr][warp] = __popc(bal);
-        }
-        __syncthreads();
-        const int rr = threadIdx.x;
-        if (rr < kRowsPerBlock && i0 + rr < m) {
-            int c = 0;
-#pragma unroll
-            for (int w = 0; w < kThreads / 32; ++w) c += s_cnt[rr][w];
-            tcounts[(i0 + rr) * ldt + tile] = c;
+        for (int r = 0; r < D; ++r) h2v[r] = H2[(int64_t)r * p + j];
+        for (int rr = 0; rr < kRowsPerBlock && i0 + rr < m; ++rr)
+            C[(i0 + rr) * ldc + j] = estimate_fixed<D, CYC>(R, b, mask, h1s[rr], h2v, reduce);
+    } else {
+        long long v[CMM_MAX_D];
+        for (int rr = 0; rr < kRowsPerBlock && i0 + rr < m; ++rr) {
+            for (int r = 0; r < d; ++r)
+                v[r] = rep_key<CYC>(R + r * b, h1s[rr][r], H2[(int64_t)r * p + j], mask);
+            C[(i0 + rr) * ldc + j] = combine_generic(v, d, reduce);
         }
     }
 }
 
-// Heavy hitters from R in one pass over the estimates (no C): the CTA of
-// extract_kernel's tile (kRowsPerBlock rows x kThreads columns) computes its
-// estimates, keeps the hits' values in shared memory, reserves room for them
-// with one atomic on a global candidate counter and writes them there in
-// (row, column) order; per (row, tile) it records the count and the offset of
-// its first candidate.  Candidates past `ccap` are dropped (the caller then
-// falls back to the two-pass count / write kernels).
-template <int D>
+// Heavy hitters in one pass over the estimates: the CTA of extract_kernel's
+// tile (kRowsPerBlock rows x kThreads columns) computes its estimates (and,
+// with WC, writes them to C as extract_kernel does), keeps the hits' values in
+// shared memory, reserves room for them with one atomic on a global candidate
+// counter and writes them there in (row, column) order; per (row, tile) it
+// records the count and the offset of its first candidate.  Candidates past
+// `ccap` are dropped (the caller then writes the list by a second pass).
+// Rows are i0 .. of this launch; H1 at stride ldh as in extract_kernel; the
+// candidates carry row0 + the row (a row block's offset in the whole C).
+template <int D, bool WC>
 __global__ void __launch_bounds__(kThreads) hh_cand_kernel(
     const double *__restrict__ R, const uint32_t *__restrict__ H1, const uint32_t *__restrict__ H2,
-    int d, int L, int64_t m, int64_t p, int reduce, HhRange hr, int32_t *__restrict__ tcounts,
+    int d, int L, int64_t m, int64_t p, int64_t ldh, int64_t row0, int reduce, HhRange hr,
+    double *__restrict__ C, int64_t ldc, int32_t *__restrict__ tcounts,
     int64_t *__restrict__ tsrc, int64_t ldt, unsigned long long *__restrict__ ncand, int64_t ccap,
     int32_t *__restrict__ CI, int32_t *__restrict__ CJ, double *__restrict__ CV) {
     __shared__ uint32_t h1s[kRowsPerBlock][CMM_MAX_D];
@@ -154,7 +125,7 @@ __global__ void __launch_bounds__(kThreads) hh_cand_kernel(
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int e = threadIdx.x; e < kRowsPerBlock * dd; e += kThreads) {
         const int rr = e / dd, r = e % dd;
-        h1s[rr][r] = (i0 + rr < m) ? H1[(int64_t)r * m + i0 + rr] : 0u;
+        h1s[rr][r] = (i0 + rr < m) ? H1[(int64_t)r * ldh + i0 + rr] : 0u;
     }
     __syncthreads();
     uint32_t hits = 0;
@@ -166,6 +137,7 @@ __global__ void __launch_bounds__(kThreads) hh_cand_kernel(
 #pragma unroll 1
             for (int rr = 0; rr < kRowsPerBlock && i0 + rr < m; ++rr) {
                 const double e = estimate_fixed<D>(R, b, mask, h1s[rr], h2v, reduce);
+                if constexpr (WC) C[(i0 + rr) * ldc + j] = e;
                 if (hh_hit(e, hr)) {
                     s_val[rr][threadIdx.x] = e;
                     hits |= 1u << rr;
@@ -177,6 +149,7 @@ __global__ void __launch_bounds__(kThreads) hh_cand_kernel(
                 for (int r = 0; r < d; ++r)
                     v[r] = rep_key(R + r * b, h1s[rr][r], H2[(int64_t)r * p + j], mask);
                 const double e = combine_generic(v, d, reduce);
+                if constexpr (WC) C[(i0 + rr) * ldc + j] = e;
                 if (hh_hit(e, hr)) {
                     s_val[rr][threadIdx.x] = e;
                     hits |= 1u << rr;
@@ -221,7 +194,7 @@ __global__ void __launch_bounds__(kThreads) hh_cand_kernel(
         if (hit) {
             const long long pos = base + s_row[rr] + s_cnt[rr][warp] + __popc(bal & ((1u << lane) - 1u));
             if (pos < ccap) {
-                CI[pos] = (int32_t)(i0 + rr);
+                CI[pos] = (int32_t)(row0 + i0 + rr);
                 CJ[pos] = (int32_t)j;
                 CV[pos] = s_val[rr][threadIdx.x];
             }
@@ -522,35 +495,24 @@ HhRange hh_range(double tau) {
 template <bool CYC>
 cudaError_t launch_extract_t(const double *R, const uint32_t *H1, const uint32_t *H2, int d, int L,
                              int64_t m, int64_t p, int reduce, double *C, int64_t ldc, int64_t ldh,
-                             HhRange hr, int32_t *tcounts, int64_t ldt, cudaStream_t s) {
+                             cudaStream_t s) {
     const int64_t blocks = ((m + kRowsPerBlock - 1) / kRowsPerBlock) * ((p + kThreads - 1) / kThreads);
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     const unsigned g = (unsigned)blocks;
-    if (tcounts) {
-        switch (d) {
-#define X(D) case D: extract_kernel<D, CYC, true><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh, hr, tcounts, ldt); break;
-            CMM_ODD_D_CASES(X)
+    switch (d) {
+#define X(D) case D: extract_kernel<D, CYC><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh); break;
+        CMM_ODD_D_CASES(X)
 #undef X
-            default: extract_kernel<0, CYC, true><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh, hr, tcounts, ldt);
-        }
-    } else {
-        switch (d) {
-#define X(D) case D: extract_kernel<D, CYC, false><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh, hr, tcounts, ldt); break;
-            CMM_ODD_D_CASES(X)
-#undef X
-            default: extract_kernel<0, CYC, false><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh, hr, tcounts, ldt);
-        }
+        default: extract_kernel<0, CYC><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_extract(const double *R, const uint32_t *H1, const uint32_t *H2, int d, int L,
                            int64_t m, int64_t p, int reduce, double *C, int64_t ldc, int64_t ldh,
-                           cudaStream_t s, int cyclic, HhRange hr, int32_t *tcounts, int64_t ldt) {
-    return cyclic ? launch_extract_t<true>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh, hr, tcounts,
-                                           ldt, s)
-                  : launch_extract_t<false>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh, hr, tcounts,
-                                            ldt, s);
+                           cudaStream_t s, int cyclic) {
+    return cyclic ? launch_extract_t<true>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh, s)
+                  : launch_extract_t<false>(R, H1, H2, d, L, m, p, reduce, C, ldc, ldh, s);
 }
 
 int64_t hh_tiles(int64_t p) { return (p + kHhTile - 1) / kHhTile; }
@@ -581,20 +543,33 @@ cudaError_t launch_hh_tile_write(const double *C, int64_t ldc, int64_t m, int64_
     return cudaGetLastError();
 }
 
-cudaError_t launch_hh_cand(const double *R, const uint32_t *H1, const uint32_t *H2, int d, int L,
-                           int64_t m, int64_t p, int reduce, HhRange hr, int32_t *tcounts,
-                           int64_t *tsrc, int64_t ldt, unsigned long long *ncand, int64_t ccap,
-                           int32_t *CI, int32_t *CJ, double *CV, cudaStream_t s) {
+template <bool WC>
+cudaError_t launch_hh_cand_t(const double *R, const uint32_t *H1, const uint32_t *H2, int d, int L,
+                             int64_t m, int64_t p, int64_t ldh, int64_t row0, int reduce,
+                             HhRange hr, double *C, int64_t ldc, int32_t *tcounts, int64_t *tsrc,
+                             int64_t ldt, unsigned long long *ncand, int64_t ccap, int32_t *CI,
+                             int32_t *CJ, double *CV, cudaStream_t s) {
     const int64_t blocks = ((m + kRowsPerBlock - 1) / kRowsPerBlock) * ((p + kThreads - 1) / kThreads);
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     const unsigned g = (unsigned)blocks;
     switch (d) {
-#define X(D) case D: hh_cand_kernel<D><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, hr, tcounts, tsrc, ldt, ncand, ccap, CI, CJ, CV); break;
+#define X(D) case D: hh_cand_kernel<D, WC><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, ldh, row0, reduce, hr, C, ldc, tcounts, tsrc, ldt, ncand, ccap, CI, CJ, CV); break;
         CMM_ODD_D_CASES(X)
 #undef X
-        default: hh_cand_kernel<0><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, reduce, hr, tcounts, tsrc, ldt, ncand, ccap, CI, CJ, CV);
+        default: hh_cand_kernel<0, WC><<<g, kThreads, 0, s>>>(R, H1, H2, d, L, m, p, ldh, row0, reduce, hr, C, ldc, tcounts, tsrc, ldt, ncand, ccap, CI, CJ, CV);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_hh_cand(const double *R, const uint32_t *H1, const uint32_t *H2, int d, int L,
+                           int64_t m, int64_t p, int64_t ldh, int64_t row0, int reduce, HhRange hr,
+                           double *C, int64_t ldc, int32_t *tcounts, int64_t *tsrc, int64_t ldt,
+                           unsigned long long *ncand, int64_t ccap, int32_t *CI, int32_t *CJ,
+                           double *CV, cudaStream_t s) {
+    return C ? launch_hh_cand_t<true>(R, H1, H2, d, L, m, p, ldh, row0, reduce, hr, C, ldc,
+                                      tcounts, tsrc, ldt, ncand, ccap, CI, CJ, CV, s)
+             : launch_hh_cand_t<false>(R, H1, H2, d, L, m, p, ldh, row0, reduce, hr, C, ldc,
+                                       tcounts, tsrc, ldt, ncand, ccap, CI, CJ, CV, s);
 }
 
 cudaError_t launch_hh_cand_copy(const int32_t *tinc, const int64_t *tsrc, int64_t ldt, int64_t m,

@@ -413,9 +413,9 @@ int run_sketch(const void *A, int64_t lda, int transA, const void *B, int64_t ld
     return CMM_OK;
 }
 
-// Decompress into C.  With hr non-null the extraction also counts, per row
-// and column tile, the estimates that pass the heavy-hitter test (into the
-// workspace's tile counts) for finish_hh.
+// Decompress into C.  With hr non-null the estimates' heavy hitters are also
+// collected on the way (launch_hh_cand writing C: counts and candidates per
+// (row, tile) in the workspace) for finish_hh.
 int run_extract(const double *R, const cmm_hashes *hs, int64_t m, int64_t p, int reduce,
                 double *C, int64_t ldc, void *ws, cudaStream_t s, int cyclic = 0,
                 const HhRange *hr = nullptr) {
@@ -428,11 +428,15 @@ int run_extract(const double *R, const cmm_hashes *hs, int64_t m, int64_t p, int
         Span sp("hash_tables", s);
         e = launch_hash_tables(hp, hs->d, hs->log2b, m, p, ew.H1, ew.H2, s);
     }
+    if (e == cudaSuccess && hr) e = cudaMemsetAsync(ew.ncand, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "hash tables");
     {
         Span sp("extract", s);
-        e = launch_extract(R, ew.H1, ew.H2, hs->d, hs->log2b, m, p, reduce, C, ldc, m, s, cyclic,
-                           hr ? *hr : HhRange{1, 0}, hr ? ew.tcounts : nullptr, ew.nt);
+        e = hr ? launch_hh_cand(R, ew.H1, ew.H2, hs->d, hs->log2b, m, p, m, 0, reduce, *hr, C, ldc,
+                                ew.tcounts, ew.tsrc, ew.nt, ew.ncand, ew.ccap, ew.CI, ew.CJ,
+                                ew.CV, s)
+               : launch_extract(R, ew.H1, ew.H2, hs->d, hs->log2b, m, p, reduce, C, ldc, m, s,
+                                cyclic);
     }
     if (e != cudaSuccess) return cuda_fail(e, "extract kernel");
     return CMM_OK;
@@ -440,10 +444,12 @@ int run_extract(const double *R, const cmm_hashes *hs, int64_t m, int64_t p, int
 
 // The heavy-hitter list of a dense C, given per-(row, tile) counts in
 // ew.tcounts: row totals (and per row the tiles' inclusive prefix), a scan
-// into offsets, each row's hits written in column order by the tiles that
-// hold them (rows past `capacity` are skipped on the device), then the total
-// is read.  One host synchronisation, at the end.
-int finish_hh(const ExtractWs &ew, const double *C, int64_t ldc, int64_t m, int64_t p,
+// into offsets, then each row's hits in column order: copied from the
+// candidates of launch_hh_cand when `cand` (read from C again for any tile
+// whose candidates did not fit), else read from C by the tiles that hold
+// them.  Rows past `capacity` are skipped on the device; one host
+// synchronisation reads the total (and the candidate count).
+int finish_hh(const ExtractWs &ew, bool cand, const double *C, int64_t ldc, int64_t m, int64_t p,
               HhRange hr, int32_t *I, int32_t *J, double *V, int64_t capacity, int64_t *count,
               cudaStream_t s) {
     cudaError_t e;
@@ -454,16 +460,29 @@ int finish_hh(const ExtractWs &ew, const double *C, int64_t ldc, int64_t m, int6
     }
     if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter scan");
     if (capacity > 0) {
-        Span sp("hh_write_dense", s);
-        e = launch_hh_tile_write(C, ldc, m, p, hr, ew.tcounts, ew.nt, ew.counts + m, I, J, V,
-                                 capacity, s);
+        Span sp(cand ? "hh_copy" : "hh_write_dense", s);
+        e = cand ? launch_hh_cand_copy(ew.tcounts, ew.tsrc, ew.nt, m, p, ew.counts + m, ew.CI,
+                                       ew.CJ, ew.CV, ew.ccap, I, J, V, capacity, s)
+                 : launch_hh_tile_write(C, ldc, m, p, hr, ew.tcounts, ew.nt, ew.counts + m, I, J,
+                                        V, capacity, s);
         if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter write");
     }
     int64_t total = 0;
+    unsigned long long ncand = 0;
     e = cudaMemcpyAsync(&total, ew.counts + 2 * m, sizeof total, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter count copy");
-    e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && cand)
+        e = cudaMemcpyAsync(&ncand, ew.ncand, sizeof ncand, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter sync");
+    if (cand && (int64_t)ncand > ew.ccap && capacity > 0) {
+        {
+            Span sp("hh_write_dense", s);
+            e = launch_hh_tile_write(C, ldc, m, p, hr, ew.tcounts, ew.nt, ew.counts + m, I, J, V,
+                                     capacity, s);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter write");
+    }
     *count = total;
     if (total > capacity)
         return fail(CMM_ERR_CAPACITY, "%lld heavy hitters, capacity %lld", (long long)total,
@@ -485,7 +504,7 @@ int run_hh_dense(const double *C, int64_t ldc, int64_t m, int64_t p, double tau,
         e = launch_hh_tile_count(C, ldc, m, p, hr, ew.tcounts, ew.nt, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter count");
-    return finish_hh(ew, C, ldc, m, p, hr, I, J, V, capacity, count, s);
+    return finish_hh(ew, false, C, ldc, m, p, hr, I, J, V, capacity, count, s);
 }
 
 // heavy hitters of the estimates from R, without writing C: one pass over the
@@ -512,8 +531,8 @@ int run_hh_R(const double *R, const cmm_hashes *hs, int64_t m, int64_t p, int re
     if (e != cudaSuccess) return cuda_fail(e, "hash tables");
     {
         Span sp("hh_candidates", s);
-        e = launch_hh_cand(R, ew.H1, ew.H2, d, L, m, p, reduce, hr, ew.tcounts, ew.tsrc, ew.nt,
-                           ew.ncand, ew.ccap, ew.CI, ew.CJ, ew.CV, s);
+        e = launch_hh_cand(R, ew.H1, ew.H2, d, L, m, p, m, 0, reduce, hr, nullptr, 0, ew.tcounts,
+                           ew.tsrc, ew.nt, ew.ncand, ew.ccap, ew.CI, ew.CJ, ew.CV, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "heavy-hitter candidates");
     {
@@ -945,8 +964,8 @@ int cmm_multiply_threshold(const void *A, int64_t lda, int32_t transA, const voi
     const HhRange hr = hh_range(tau);
     rc = run_extract(Rw, hs, m, p, reduce, C, ldc, scratch, s, 0, &hr);
     if (rc) return rc;
-    return finish_hh(carve_extract(scratch, m, p, hs->d), C, ldc, m, p, hr, I, J, V, capacity,
-                     count, s);
+    return finish_hh(carve_extract(scratch, m, p, hs->d), true, C, ldc, m, p, hr, I, J, V,
+                     capacity, count, s);
 }
 
 namespace {
@@ -1145,6 +1164,8 @@ int cmm_multiply_host(const void *A, int64_t lda, int32_t transA, const void *B,
             Span sp("hash_tables", s);
             e = launch_hash_tables(hp, hs->d, hs->log2b, m, p, ew.H1, ew.H2, s);
         }
+        if (e == cudaSuccess && count)
+            e = cudaMemsetAsync(ew.ncand, 0, sizeof(unsigned long long), s);
         if (e != cudaSuccess) return cuda_fail(e, "hash tables");
         const int nrb = host_row_blocks(m, p);
         for (int i = 0; i < nrb; ++i) {
@@ -1152,9 +1173,12 @@ int cmm_multiply_host(const void *A, int64_t lda, int32_t transA, const void *B,
             if (mb == 0) continue;
             {
                 Span sp("extract", s);
-                e = launch_extract(Rw, ew.H1 + i0, ew.H2, hs->d, hs->log2b, mb, p, reduce,
-                                   dC + i0 * p, p, m, s, 0, hr,
-                                   count ? ew.tcounts + i0 * ew.nt : nullptr, ew.nt);
+                e = count ? launch_hh_cand(Rw, ew.H1 + i0, ew.H2, hs->d, hs->log2b, mb, p, m, i0,
+                                           reduce, hr, dC + i0 * p, p, ew.tcounts + i0 * ew.nt,
+                                           ew.tsrc + i0 * ew.nt, ew.nt, ew.ncand, ew.ccap, ew.CI,
+                                           ew.CJ, ew.CV, s)
+                          : launch_extract(Rw, ew.H1 + i0, ew.H2, hs->d, hs->log2b, mb, p,
+                                           reduce, dC + i0 * p, p, m, s);
             }
             if (e != cudaSuccess) return cuda_fail(e, "extract kernel");
             if (C) {
@@ -1171,8 +1195,8 @@ int cmm_multiply_host(const void *A, int64_t lda, int32_t transA, const void *B,
     }
     int hh_rc = CMM_OK;
     if (count && m > 0 && p > 0) {
-        hh_rc = finish_hh(carve_extract(scratch, m, p, hs->d), dC, p, m, p, hr, dI, dJ, dV, cap,
-                          count, s);
+        hh_rc = finish_hh(carve_extract(scratch, m, p, hs->d), true, dC, p, m, p, hr, dI, dJ, dV,
+                          cap, count, s);
         if (hh_rc != CMM_OK && hh_rc != CMM_ERR_CAPACITY) return hh_rc;
         const int64_t n = std::min(*count, cap);
         if (n > 0) {
