@@ -136,9 +136,11 @@ int cmm_extract(const double *R, const cmm_hashes *hs, int64_t m, int64_t p, int
 /* Heavy hitters straight from the sketch (the goal of the method, Sec. 1):
  * every (i, j) with |Chat[i][j]| >= tau, sorted by (i, j) row-major, written to
  * I, J (device int32) and V (device FP64, the estimate) up to `capacity`
- * entries.  *count (HOST) receives the total number found.  Synchronises
- * `stream` to read the count.  Returns CMM_ERR_CAPACITY when *count >
- * capacity (the first `capacity` entries are still written). */
+ * entries, without writing Chat: one pass over the estimates (a second when
+ * there are more hits than one per 64 entries).  *count (HOST) receives the
+ * total number found.  Synchronises `stream` to read the count.  Returns
+ * CMM_ERR_CAPACITY when *count > capacity (the first `capacity` entries are
+ * still written). */
 int cmm_heavy_hitters(const double *R, const cmm_hashes *hs, int64_t m, int64_t p,
                       int32_t reduce, double tau, int32_t *I, int32_t *J, double *V,
                       int64_t capacity, int64_t *count, void *ws, size_t ws_bytes,
@@ -163,13 +165,14 @@ int cmm_multiply(const void *A, int64_t lda, int32_t transA, const void *B, int6
                  int32_t prec, int32_t reduce, double *C, int64_t ldc, double *R,
                  void *ws, size_t ws_bytes, void *stream);
 
-/* cmm_multiply followed by cmm_threshold(C, tau) in one call, with the
- * per-row heavy-hitter counts taken while Decompress writes C (Algorithm 1's
- * Decompress, then the goal of Sec. 1), so the list costs one ordered pass
- * over C instead of two.  Outputs as cmm_multiply (C, R) plus the list of
- * cmm_threshold: I, J (device int32), V (device FP64), `capacity` entries,
- * *count (HOST) = total found.  Synchronises `stream` to read the count.
- * `ws`: cmm_multiply_workspace_bytes.  Errors: as cmm_multiply, plus
+/* cmm_multiply followed by cmm_threshold(C, tau) in one call (Algorithm 1's
+ * Decompress, then the goal of Sec. 1): the heavy hitters are collected while
+ * Decompress writes C, so the list costs no further pass over C (one pass
+ * when there are more hits than one per 64 entries of C).  Outputs as
+ * cmm_multiply (C, R) plus the list of cmm_threshold: I, J (device int32), V
+ * (device FP64), `capacity` entries, *count (HOST) = total found.
+ * Synchronises `stream` to read the count.  `ws`:
+ * cmm_multiply_workspace_bytes.  Errors: as cmm_multiply, plus
  * CMM_ERR_CAPACITY as in cmm_threshold. */
 int cmm_multiply_threshold(const void *A, int64_t lda, int32_t transA, const void *B,
                            int64_t ldb, int32_t dtype, int64_t m, int64_t k, int64_t p,
