@@ -97,7 +97,7 @@ cudaError_t launch_convert_out(const void *src, int src_f64, int64_t rows, int64
 // Record `msg` as the calling thread's cmm_last_error() text; returns `code`.
 int set_error(int code, const char *msg);
 
-// ---- launchers (sketch.cu / sketch_f64.cu / finish.cu) ----
+// ---- launchers (prep.cu, sketch_f32.cu, sketch_f64.cu, sketch_tm.cu, sketch_bf16.cu, finish.cu) ----
 // A^T (k x m) and B (k x p) in the butterfly type.  With FP32 output and rmax
 // non-null, also rmax[t] = max(rmax[t], max |row t of the output|) (rmax
 // zeroed by the caller): the row maxima of launch_rowmax without a second read.
