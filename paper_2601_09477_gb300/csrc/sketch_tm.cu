@@ -153,12 +153,13 @@ __device__ __forceinline__ void tm_fwht(float *S, float (&v)[kTmE], int q, float
     for (int c = 0; c < kTmE / 4; ++c)
         row[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
     __syncthreads();
+    // each word of this thread's column is read and zeroed for the next
+    // scatter by one exchange (a warp's 32 lanes hit 32 distinct banks, and an
+    // exchange costs the shared-memory pipe about what a load does, so this
+    // replaces a load pass, a clearing pass and a barrier)
+    int *Si = reinterpret_cast<int *>(S);
 #pragma unroll
-    for (int j = 0; j < kTmE; ++j) v[j] = S[q + 132 * j];
-    // every column has been read: clear this thread's row for the next scatter
-    __syncthreads();
-#pragma unroll
-    for (int c = 0; c < kTmE / 4; ++c) row[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int j = 0; j < kTmE; ++j) v[j] = __int_as_float(atomicExch(Si + q + 132 * j, 0));
     reg_fwht_f32<kTmE, kTmLE>(v);
 }
 
