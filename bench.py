@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--log2b", type=int, default=16)
     ap.add_argument("--d", type=int, default=9)
-    ap.add_argument("--prec", default="f32", choices=["f32", "f64", "bf16tc"])
+    ap.add_argument("--prec", default="f32", choices=["f32", "f64", "bf16tc", "f16tc"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-dgemm", action="store_true", help="skip the cuBLAS DGEMM comparison")
     ap.add_argument("--no-e2e", action="store_true")
@@ -553,8 +553,9 @@ def batched_oracle(raw, probs, d, nsample=8):
 
 
 def run_precision(a):
-    """n=16384, b=2^18, d=7: FP32 and BF16 tensor-core butterflies (and one
-    plain FP64 step) on the same input; errors of R against the FP64 form."""
+    """n=16384, b=2^18, d=7: FP32 butterflies and BF16 / FP16 tensor-core
+    Hadamard blocks (and one plain FP64 step) on the same input; errors of R
+    against the FP64 form."""
     import torch
     from paper_2601_09477_gb300 import cmm
     from paper_2601_09477_gb300 import workloads as wl
@@ -563,12 +564,13 @@ def run_precision(a):
     A, B, S = wl.orthogonal_precision(n=n, seed=1003, device="cuda")
     h = cmm.make_hashes(2003, d, L)
     ws = torch.empty(max(cmm.multiply_workspace_bytes(n, n, n, h, torch.float32, p)
-                         for p in ("f32", "bf16tc", "f64")), dtype=torch.uint8, device="cuda")
+                         for p in ("f32", "bf16tc", "f16tc", "f64")), dtype=torch.uint8,
+                     device="cuda")
     C = torch.empty((n, n), dtype=torch.float64, device="cuda")
     Rs, times, kernels = {}, {}, {}
     clocks = ClockSampler(0)
     clocks.start()
-    for prec, reps in (("f64", 1), ("f32", a.steps), ("bf16tc", a.steps)):
+    for prec, reps in (("f64", 1), ("f32", a.steps), ("bf16tc", a.steps), ("f16tc", a.steps)):
         R = torch.empty((d, 1 << L), dtype=torch.float64, device="cuda")
         fn = lambda: cmm.multiply(A, B, h, prec=prec, R=R, out=C, ws=ws)
         for _ in range(1 if prec == "f64" else a.warmup):
@@ -582,7 +584,8 @@ def run_precision(a):
     clk = clocks.stop()
     scale = float((torch.linalg.vector_norm(A.double(), dim=0) *
                    torch.linalg.vector_norm(B.double(), dim=1)).sum().item())
-    err = {p: float((Rs[p] - Rs["f64"]).abs().max().item() / scale) for p in ("f32", "bf16tc")}
+    low = ("f32", "bf16tc", "f16tc")
+    err = {p: float((Rs[p] - Rs["f64"]).abs().max().item() / scale) for p in low}
     rms = float(Rs["f64"].pow(2).mean().sqrt().item())
     res = {"metric": "precision workload: multiply ms per precision, R error vs the FP64 form",
            "value": times["bf16tc"], "unit": "ms", "n_gpus": 1, "steps": a.steps,
@@ -591,8 +594,8 @@ def run_precision(a):
                                   "N(0,1)*100, b=2^18, d=7, FP32 storage"},
            "ms": times, "R_err_rel_to_sum_norms": err,
            "R_err_rel_to_rms": {p: float((Rs[p] - Rs["f64"]).abs().max().item() / rms)
-                                for p in ("f32", "bf16tc")},
-           "speedup_vs_fp64": {p: round(times["f64"] / times[p], 2) for p in ("f32", "bf16tc")},
+                                for p in low},
+           "speedup_vs_fp64": {p: round(times["f64"] / times[p], 2) for p in low},
            "kernels_ms_per_call": kernels, "clocks": clk,
            "roofline": alu_roofline("sketch_f32", d * n * (2.0 * (1 << L) * L + (1 << L)),
                                     kernels["f32"].get("sketch_f32", float("nan")),

@@ -62,7 +62,8 @@ typedef enum { CMM_F64 = 0, CMM_F32 = 1, CMM_BF16 = 2 } cmm_dtype;
 typedef enum {
     CMM_PREC_F64 = 0,     /* FP64 butterflies and accumulation ("plain FP64") */
     CMM_PREC_F32 = 1,     /* FP32 butterflies, FP32 accumulation within a block of t */
-    CMM_PREC_BF16TC = 2   /* BF16 operands with exact +-1 Hadamard blocks on the tensor cores, FP32 accumulation */
+    CMM_PREC_BF16TC = 2,  /* BF16 operands with exact +-1 Hadamard blocks on the tensor cores, FP32 accumulation */
+    CMM_PREC_F16TC = 3    /* as BF16TC with FP16 operands, scaled to a fixed range (3 more significand bits) */
 } cmm_prec;
 
 /* how the d repetitions are combined */

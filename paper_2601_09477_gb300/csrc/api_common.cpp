@@ -111,7 +111,7 @@ bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int p
     pl.prec = prec;
     pl.L = L;
     const bool f64 = prec == CMM_PREC_F64;
-    const bool bf16 = prec == CMM_PREC_BF16TC;
+    const bool bf16 = prec_tc(prec);
     if (bf16 && L < sketch_bf16_llo()) return false;
     const int maxLlo = bf16 ? sketch_bf16_llo() : (f64 ? kMaxLloF64 : kMaxLloF32);
     pl.Llo = std::min(L, maxLlo);
@@ -210,7 +210,7 @@ int check_operands(const void *A, int64_t lda, int transA, const void *B, int64_
     int rc = check_sizes(m, k, p);
     if (rc) return rc;
     if (!valid_dtype(dtype)) return fail(CMM_ERR_ARG, "bad dtype %d", dtype);
-    if (prec != CMM_PREC_F64 && prec != CMM_PREC_F32 && prec != CMM_PREC_BF16TC)
+    if (prec != CMM_PREC_F64 && prec != CMM_PREC_F32 && !prec_tc(prec))
         return fail(CMM_ERR_ARG, "bad precision %d", prec);
     if (transA != 0 && transA != 1) return fail(CMM_ERR_ARG, "transA must be 0 or 1");
     if (m > 0 && k > 0 && !A) return fail(CMM_ERR_ARG, "A is NULL");
@@ -344,14 +344,17 @@ int run_sketch(const void *A, int64_t lda, int transA, const void *B, int64_t ld
                                  tabB, cm, pc, s);
         } else {
             // these launchers build their scatter tables first (two launches)
-            Span sp(prec == CMM_PREC_F64 ? "sketch_f64"
-                    : prec == CMM_PREC_BF16TC ? "sketch_bf16tc" : "sketch_f32", s, 2);
+            Span sp(prec == CMM_PREC_F64       ? "sketch_f64"
+                    : prec == CMM_PREC_BF16TC ? "sketch_bf16tc"
+                    : prec == CMM_PREC_F16TC  ? "sketch_f16tc"
+                                              : "sketch_f32",
+                    s, 2);
             if (prec == CMM_PREC_F64)
                 e = launch_sketch_f64(pp, (const double *)Atc, (const double *)Bpc, m, kp, p,
                                       hs->d, hp, tabA, tabB, nullptr, pc, s);
-            else if (prec == CMM_PREC_BF16TC)
+            else if (prec_tc(prec))
                 e = launch_sketch_bf16(pp, (const float *)Atc, (const float *)Bpc, m, kp, p, hs->d,
-                                       hp, tabA, tabB, cm, pc, s);
+                                       hp, tabA, tabB, cm, pc, prec == CMM_PREC_F16TC, s);
             else
                 e = launch_sketch_f32(pp, (const float *)Atc, (const float *)Bpc, m, kp, p, hs->d,
                                       hp, tabA, tabB, cm, pc, s);

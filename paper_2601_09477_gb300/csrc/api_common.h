@@ -62,6 +62,8 @@ int num_sms();
 int check_hashes(const cmm_hashes *hs);
 void fill_params(const cmm_hashes *hs, HashParams &hp);
 bool valid_dtype(int dt);
+// the 16-bit tensor-core precisions (BF16 or FP16 operands)
+inline bool prec_tc(int prec) { return prec == CMM_PREC_BF16TC || prec == CMM_PREC_F16TC; }
 size_t dtype_size(int dt);
 int check_sizes(int64_t m, int64_t k, int64_t p);
 bool use_tmem_kernel();

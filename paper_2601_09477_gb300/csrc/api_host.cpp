@@ -45,7 +45,7 @@ int host_parts(int64_t m, int64_t k, int64_t p, size_t es) {
 double host_part_ratio(int64_t m, int64_t p, int d, int L, size_t es, int prec) {
     const double b = std::ldexp(1.0, L);
     const double copy_t = (double)(m + p) * (double)es / 211e9;
-    const double rate = prec == CMM_PREC_F64 ? 0.45e12 : prec == CMM_PREC_BF16TC ? 13e12 : 18e12;
+    const double rate = prec == CMM_PREC_F64 ? 0.45e12 : prec_tc(prec) ? 13e12 : 18e12;
     const double sketch_t = (double)d * (2.0 * b * L + b) / rate;
     return std::min(3.0, std::max(0.5, sketch_t / copy_t));
 }
@@ -129,8 +129,8 @@ int cmm_multiply_host(const void *A, int64_t lda, int32_t transA, const void *B,
     if (rc) return rc;
     rc = check_operands(A, lda, transA, B, ldb, dtype, m, k, p, prec);
     if (rc) return rc;
-    if (prec == CMM_PREC_BF16TC && hs->log2b < sketch_bf16_llo())
-        return fail(CMM_ERR_RANGE, "precision BF16TC needs log2b >= %d", sketch_bf16_llo());
+    if (prec_tc(prec) && hs->log2b < sketch_bf16_llo())
+        return fail(CMM_ERR_RANGE, "the tensor-core precisions need log2b >= %d", sketch_bf16_llo());
     if (reduce != CMM_MEDIAN && reduce != CMM_MEAN) return fail(CMM_ERR_ARG, "bad reduce %d", reduce);
     if (C && ldc < p) return fail(CMM_ERR_ARG, "ldc = %lld < p", (long long)ldc);
     if (count && capacity < 0) return fail(CMM_ERR_ARG, "negative capacity");

@@ -136,14 +136,15 @@ cudaError_t launch_sketch_tm_tables(const SketchPlan &pl, int64_t m, int64_t p, 
 cudaError_t launch_sketch_tm(const SketchPlan &pl, const float *At, const float *Bp, int64_t m,
                              int64_t k, int64_t p, int d, const tab_t *tabA, const tab_t *tabB,
                              const float *colmax, double *partial, cudaStream_t s);
-// BF16 tensor-core variant (2^15-point slices, fixed-point scatter; colmax as
-// for the FP32 kernels)
+// 16-bit tensor-core variant (2^15-point slices, fixed-point scatter; colmax as
+// for the FP32 kernels): BF16 operands, or FP16 operands with f16
 int sketch_bf16_llo();
 int sketch_bf16_threads();
 size_t sketch_bf16_smem();
 cudaError_t launch_sketch_bf16(const SketchPlan &pl, const float *At, const float *Bp, int64_t m,
                                int64_t k, int64_t p, int d, const HashParams &hp, tab_t *tabA,
-                               tab_t *tabB, const float *colmax, double *partial, cudaStream_t s);
+                               tab_t *tabB, const float *colmax, double *partial, bool f16,
+                               cudaStream_t s);
 // cyclic (FFT) form of Sec. 3.1: 2^13-frequency classes, 32-bit tables of
 // d * nclass * m and d * nclass * p words (built by the launcher), complex FP64
 // partials [block][r][class][2^13][2]; the finish writes G [r][C][2^13][2]

@@ -1,4 +1,5 @@
-// sketch_bf16.cu -- the sketch with BF16 tensor-core Hadamard blocks.
+// sketch_bf16.cu -- the sketch with 16-bit tensor-core Hadamard blocks (BF16
+// or FP16 operands).
 //
 // Same work item as the FP32 kernels (Algorithm 1's loop over t, frequency
 // split, FP64 partial per block of t), for 2^15-point slices.  The transform
@@ -13,12 +14,22 @@
 //                      n = e + 2 f becomes H16 X2 (H8 (x) I2): bits 8-11 by
 //                      H16, bits 12-14 by H8 while bit 0 (already transformed
 //                      in pass 1) passes through the identity factor.
-// H16, H8 (x) I2 hold only 0 and +-1, exact in BF16.  The scatter is the
+// H16, H8 (x) I2 hold only 0 and +-1, exact in BF16 and FP16.  The scatter is the
 // fixed-point integer scatter of the FP32 kernels (per-column power-of-two
 // scale, exact bucket sums); rounding happens where a value becomes a BF16
 // operand: once per bucket when pass 1 reads the integer slice, the product
 // inputs of pass 2, and the slice between the passes.  H x_t and the running
 // sum Z stay FP32 in tensor memory (TMEM), one lane per thread.
+//
+// FP16 operands (template flag F16) carry 3 more significand bits than BF16
+// but only 5 exponent bits, so they are scaled to a fixed range instead of
+// holding real values: the integer bucket sums (|sum| < 2^30 + c_max / 2, see
+// bf_scale) enter as sum * 2^-27 (< 8), the largest value that becomes an FP16
+// operand is the pass-2 intermediate after 12 butterfly bits (< 2^15, below
+// FP16's largest finite 65504), and each FP32 output is multiplied back by
+// 2^27 and by the column scale 2^-e.  Values below 2^-14 in the scaled units
+// (2^-17 of the bound) are FP16 subnormals and keep an absolute error of
+// 2^-25 there.
 //
 // Shared memory: the integer slice (2^15 words, element u at word
 // u ^ (((u >> 4) & 3) << 3): pass 1's 64-bit loads of a half-warp hit 32
@@ -27,6 +38,7 @@
 // bank-conflict free, pass-1 stores 2-way conflicted; fully rewritten by every
 // pass 1, so never cleared).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "cmm_internal.h"
 #include "fwht_device.cuh"
@@ -60,24 +72,51 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t *>(&v);
+template <bool F16>
+__device__ __forceinline__ uint32_t pack16(float lo, float hi) {
+    if constexpr (F16) {
+        __half2 v = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<uint32_t *>(&v);
+    } else {
+        __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<uint32_t *>(&v);
+    }
+}
+
+// one value rounded to the operand type, as its 16 bits
+template <bool F16>
+__device__ __forceinline__ uint16_t bits16(float x) {
+    if constexpr (F16) {
+        __half v = __float2half_rn(x);
+        return *reinterpret_cast<uint16_t *>(&v);
+    } else {
+        __nv_bfloat16 v = __float2bfloat16_rn(x);
+        return *reinterpret_cast<uint16_t *>(&v);
+    }
 }
 
 __device__ __forceinline__ float hsign(int i, int j) {
     return (__popc(i & j) & 1) ? -1.f : 1.f;
 }
 
-// D (16x8, FP32) = A (16x16, BF16) . B (16x8, BF16)
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4],
-                                         const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%10,%11,%12,%13};"
-        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "f"(0.f), "f"(0.f),
-          "f"(0.f), "f"(0.f));
+// D (16x8, FP32) = A (16x16) . B (16x8), both operands BF16 or both FP16
+template <bool F16>
+__device__ __forceinline__ void mma16(float (&d)[4], const uint32_t (&a)[4],
+                                      const uint32_t (&b)[2]) {
+    if constexpr (F16)
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 "
+            "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%10,%11,%12,%13};"
+            : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "f"(0.f),
+              "f"(0.f), "f"(0.f), "f"(0.f));
+    else
+        asm volatile(
+            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+            "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%10,%11,%12,%13};"
+            : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+            : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "f"(0.f),
+              "f"(0.f), "f"(0.f), "f"(0.f));
 }
 
 __device__ __forceinline__ void tmem_st8(uint32_t addr, const float (&x)[8]) {
@@ -115,48 +154,63 @@ __device__ __forceinline__ float m2(int k, int n) {
     return ((k & 1) == (n & 1)) ? hsign(k >> 1, n >> 1) : 0.f;
 }
 
+template <bool F16>
 __device__ __forceinline__ void make_frags(HFrags &f, int g, int c) {
     // A fragment: (row g, k 2c..2c+1), (row g+8, k 2c..), (row g, k 2c+8..), (row g+8, k 2c+8..)
-    f.hA[0] = pack_bf16(hsign(g, 2 * c), hsign(g, 2 * c + 1));
-    f.hA[1] = pack_bf16(hsign(g + 8, 2 * c), hsign(g + 8, 2 * c + 1));
-    f.hA[2] = pack_bf16(hsign(g, 2 * c + 8), hsign(g, 2 * c + 9));
-    f.hA[3] = pack_bf16(hsign(g + 8, 2 * c + 8), hsign(g + 8, 2 * c + 9));
+    f.hA[0] = pack16<F16>(hsign(g, 2 * c), hsign(g, 2 * c + 1));
+    f.hA[1] = pack16<F16>(hsign(g + 8, 2 * c), hsign(g + 8, 2 * c + 1));
+    f.hA[2] = pack16<F16>(hsign(g, 2 * c + 8), hsign(g, 2 * c + 9));
+    f.hA[3] = pack16<F16>(hsign(g + 8, 2 * c + 8), hsign(g + 8, 2 * c + 9));
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int n = 8 * h + g;   // B fragment: (k 2c..2c+1, col n), (k 2c+8..2c+9, col n)
-        f.hB[h][0] = pack_bf16(hsign(2 * c, n), hsign(2 * c + 1, n));
-        f.hB[h][1] = pack_bf16(hsign(2 * c + 8, n), hsign(2 * c + 9, n));
-        f.mB[h][0] = pack_bf16(m2(2 * c, n), m2(2 * c + 1, n));
-        f.mB[h][1] = pack_bf16(m2(2 * c + 8, n), m2(2 * c + 9, n));
+        f.hB[h][0] = pack16<F16>(hsign(2 * c, n), hsign(2 * c + 1, n));
+        f.hB[h][1] = pack16<F16>(hsign(2 * c + 8, n), hsign(2 * c + 9, n));
+        f.mB[h][0] = pack16<F16>(m2(2 * c, n), m2(2 * c + 1, n));
+        f.mB[h][1] = pack16<F16>(m2(2 * c + 8, n), m2(2 * c + 9, n));
     }
 }
 
 // one tile: D2 = (H16 . X) . Bop for the two column halves.  xb[h] are the
 // B-operand fragments of X (column half h); d2[h] the output fragments.
+template <bool F16>
 __device__ __forceinline__ void tile_pass(const HFrags &f, const uint32_t (&xb)[2][2],
                                           const uint32_t (&bop)[2][2], float (&d2)[2][4]) {
     float d1[2][4];
-    mma_bf16(d1[0], f.hA, xb[0]);
-    mma_bf16(d1[1], f.hA, xb[1]);
+    mma16<F16>(d1[0], f.hA, xb[0]);
+    mma16<F16>(d1[1], f.hA, xb[1]);
     // accumulator fragments of D1 = A-operand fragment of D1 (rows g / g+8, k = columns)
-    const uint32_t a[4] = {pack_bf16(d1[0][0], d1[0][1]), pack_bf16(d1[0][2], d1[0][3]),
-                           pack_bf16(d1[1][0], d1[1][1]), pack_bf16(d1[1][2], d1[1][3])};
-    mma_bf16(d2[0], a, bop[0]);
-    mma_bf16(d2[1], a, bop[1]);
+    const uint32_t a[4] = {pack16<F16>(d1[0][0], d1[0][1]), pack16<F16>(d1[0][2], d1[0][3]),
+                           pack16<F16>(d1[1][0], d1[1][1]), pack16<F16>(d1[1][2], d1[1][3])};
+    mma16<F16>(d2[0], a, bop[0]);
+    mma16<F16>(d2[1], a, bop[1]);
 }
 
-// two integer bucket sums -> FP32 (scaled by inv) -> packed BF16 pair
-__device__ __forceinline__ uint32_t int2_to_bf16x2(int2 w, float inv) {
-    return pack_bf16(__int2float_rn(w.x) * inv, __int2float_rn(w.y) * inv);
+// FP16 operands: the integer bucket sums enter as sum * 2^-27 (see the header)
+constexpr float kF16In = 1.0f / 134217728.0f;    // 2^-27
+constexpr float kF16Out = 134217728.0f;          // 2^27
+
+// two integer bucket sums -> FP32 -> packed 16-bit pair: real values (sum *
+// inv) for BF16, sum * 2^-27 for FP16
+template <bool F16>
+__device__ __forceinline__ uint32_t int2_to_16x2(int2 w, float inv) {
+    const float sc = F16 ? kF16In : inv;
+    return pack16<F16>(__int2float_rn(w.x) * sc, __int2float_rn(w.y) * sc);
+}
+
+// an FP32 transform output in real units (FP16: undo the 2^-27 and apply the
+// column scale; two multiplies so that no factor overflows)
+template <bool F16>
+__device__ __forceinline__ float out_real(float v, float inv) {
+    return F16 ? (v * kF16Out) * inv : v;
 }
 
 // the 2^15-point transform of the slice; `sink(i, vals)` receives, for the
 // warp's i-th pass-2 tile, the 8 FP32 outputs of this thread.  Pass 1 reads
 // (and clears) the integer slice Si, scaled by inv.
-template <typename Sink>
-__device__ __forceinline__ void bf_fwht(int *Si, __nv_bfloat16 *S, const HFrags &f, int warp,
+template <bool F16, typename Sink>
+__device__ __forceinline__ void bf_fwht(int *Si, uint16_t *S16, const HFrags &f, int warp,
                                         int g, int c, float inv, Sink sink) {
-    uint16_t *S16 = reinterpret_cast<uint16_t *>(S);
     // pass 1: tiles tau = warp * 8 + i, u = a + 16 b + 256 tau
 #pragma unroll 2
     for (int i = 0; i < kBTilesPerWarp; ++i) {
@@ -171,11 +225,11 @@ __device__ __forceinline__ void bf_fwht(int *Si, __nv_bfloat16 *S, const HFrags 
             const int2 w0 = *p0, w1 = *p1;
             *p0 = make_int2(0, 0);
             *p1 = make_int2(0, 0);
-            xb[h][0] = int2_to_bf16x2(w0, inv);
-            xb[h][1] = int2_to_bf16x2(w1, inv);
+            xb[h][0] = int2_to_16x2<F16>(w0, inv);
+            xb[h][1] = int2_to_16x2<F16>(w1, inv);
         }
         float d2[2][4];
-        tile_pass(f, xb, f.hB, d2);
+        tile_pass<F16>(f, xb, f.hB, d2);
         // d2[h]: rows a' = g (regs 0,1) / g + 8 (regs 2,3), columns b' = 8h + 2c (+1)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -183,8 +237,7 @@ __device__ __forceinline__ void bf_fwht(int *Si, __nv_bfloat16 *S, const HFrags 
             for (int rr = 0; rr < 4; ++rr) {
                 const int ap = g + 8 * (rr >> 1);
                 const int bp = 8 * h + 2 * c + (rr & 1);
-                __nv_bfloat16 v = __float2bfloat16_rn(d2[h][rr]);
-                S16[bf_pad(ap + 16 * bp + 256 * tau)] = *reinterpret_cast<uint16_t *>(&v);
+                S16[bf_pad(ap + 16 * bp + 256 * tau)] = bits16<F16>(d2[h][rr]);
             }
         }
     }
@@ -208,12 +261,12 @@ __device__ __forceinline__ void bf_fwht(int *Si, __nv_bfloat16 *S, const HFrags 
             xb[h][1] = vc | (vd << 16);
         }
         float d2[2][4];
-        tile_pass(f, xb, f.mB, d2);
+        tile_pass<F16>(f, xb, f.mB, d2);
         float vals[8];
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
-            for (int rr = 0; rr < 4; ++rr) vals[4 * h + rr] = d2[h][rr];
+            for (int rr = 0; rr < 4; ++rr) vals[4 * h + rr] = out_real<F16>(d2[h][rr], inv);
         sink(i, vals);
     }
 }
@@ -311,6 +364,7 @@ __device__ __forceinline__ void bf_scale(float colmax, int cmax, float &s, float
     inv = __int_as_float((127 - e) << 23);
 }
 
+template <bool F16>
 __global__ void __launch_bounds__(kBThreads, 1)
 sketch_bf16_kernel(const float *__restrict__ At, int64_t ldat, const float *__restrict__ Bp,
                    int64_t ldbp, int64_t m, int64_t k, int64_t p, int Lfull, int C, int64_t chunk,
@@ -318,7 +372,7 @@ sketch_bf16_kernel(const float *__restrict__ At, int64_t ldat, const float *__re
                    const float *__restrict__ colmax, double *__restrict__ partial, int vec4) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int *Si = reinterpret_cast<int *>(smem_raw);
-    __nv_bfloat16 *S = reinterpret_cast<__nv_bfloat16 *>(smem_raw + kBIntBytes);
+    uint16_t *S = reinterpret_cast<uint16_t *>(smem_raw + kBIntBytes);
     uint32_t *s_taddr = reinterpret_cast<uint32_t *>(smem_raw + kBIntBytes + kBBfBytes);
     int *s_red = reinterpret_cast<int *>(smem_raw + kBIntBytes + kBBfBytes + 16);
     const int q = threadIdx.x, warp = q >> 5, lane = q & 31;
@@ -355,7 +409,7 @@ sketch_bf16_kernel(const float *__restrict__ At, int64_t ldat, const float *__re
     const uint32_t tx = *s_taddr + ((uint32_t)(32 * (warp & 3)) << 16) + 128u * (uint32_t)(warp >> 2);
     const uint32_t tz = tx + 64;
     HFrags f;
-    make_frags(f, g, c);
+    make_frags<F16>(f, g, c);
     {
         float zero[8];
 #pragma unroll
@@ -370,12 +424,12 @@ sketch_bf16_kernel(const float *__restrict__ At, int64_t ldat, const float *__re
         bf_scale(__ldg(colmax + k + t), cmaxB, sB, invB);
         scatter_bf16(Si, At + t * ldat, tA, m, q, sA, vec4);
         __syncthreads();
-        bf_fwht(Si, S, f, warp, g, c, invA,
+        bf_fwht<F16>(Si, S, f, warp, g, c, invA,
                 [&](int i, const float(&vals)[8]) { tmem_st8(tx + 8 * i, vals); });
         __syncthreads();
         scatter_bf16(Si, Bp + t * ldbp, tB, p, q, sB, vec4);
         __syncthreads();
-        bf_fwht(Si, S, f, warp, g, c, invB, [&](int i, const float(&vals)[8]) {
+        bf_fwht<F16>(Si, S, f, warp, g, c, invB, [&](int i, const float(&vals)[8]) {
             float xs[8], zs[8];
             tmem_ld8(tx + 8 * i, xs);
             tmem_ld8(tz + 8 * i, zs);
@@ -439,7 +493,8 @@ size_t sketch_bf16_smem() { return kBSmem; }
 
 cudaError_t launch_sketch_bf16(const SketchPlan &pl, const float *At, const float *Bp, int64_t m,
                                int64_t k, int64_t p, int d, const HashParams &hp, tab_t *tabA,
-                               tab_t *tabB, const float *colmax, double *partial, cudaStream_t s) {
+                               tab_t *tabB, const float *colmax, double *partial, bool f16,
+                               cudaStream_t s) {
     const int64_t n = (int64_t)d * pl.C * (m + p);
     int64_t gsz = (n + 255) / 256;
     if (gsz > 152 * 32) gsz = 152 * 32;
@@ -447,8 +502,8 @@ cudaError_t launch_sketch_bf16(const SketchPlan &pl, const float *At, const floa
     bf16_table_kernel<<<(unsigned)gsz, 256, 0, s>>>(hp, d, pl.L, pl.C, m, p, tabA, tabB);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(sketch_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kBSmem);
+    auto kern = f16 ? sketch_bf16_kernel<true> : sketch_bf16_kernel<false>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBSmem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (int64_t)pl.nchunks * d * pl.C;
     const bool vec4 = m % 4 == 0 && p % 4 == 0 && pl.ldat % 4 == 0 && pl.ldbp % 4 == 0 &&
@@ -456,7 +511,7 @@ cudaError_t launch_sketch_bf16(const SketchPlan &pl, const float *At, const floa
                       reinterpret_cast<uintptr_t>(Bp) % 16 == 0 &&
                       reinterpret_cast<uintptr_t>(tabA) % 8 == 0 &&
                       reinterpret_cast<uintptr_t>(tabB) % 8 == 0;
-    sketch_bf16_kernel<<<(unsigned)blocks, kBThreads, kBSmem, s>>>(
+    kern<<<(unsigned)blocks, kBThreads, kBSmem, s>>>(
         At, pl.ldat, Bp, pl.ldbp, m, k, p, pl.L, pl.C, pl.chunk, d, tabA, tabB, colmax, partial,
         vec4 ? 1 : 0);
     return cudaGetLastError();

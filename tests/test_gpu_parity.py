@@ -111,32 +111,70 @@ def test_fp32_sketch_is_deterministic(cmm, L):
     assert torch.equal(R1, R2)
 
 
+# tensor-core precisions: (max |R - R_orc| / sum_t ||A_t|| ||B_t||, max |R - R_orc| / max |R_orc|).
+# BF16 keeps 8 significand bits, FP16 11: the FP16 bounds are the BF16 ones
+# divided by 8 (the ratio of their unit roundoffs), the second rounded up to 1e-2.
+TC_TOL = {"bf16tc": (2e-2, 0.05), "f16tc": (2.5e-3, 0.01)}
+
+
+def _tc_error(cmm, A, B, h, L, prec):
+    R = cmm.sketch(_dev(A, torch.float32), _dev(B, torch.float32), h, prec=prec).cpu().numpy()
+    A32 = A.astype(np.float32).astype(np.float64)
+    B32 = B.astype(np.float32).astype(np.float64)
+    Ro = orc.compress(A32, B32, h.params, L, nthreads=8)
+    dR = np.abs(R - Ro).max()
+    return dR / _norm_scale(A32, B32), dR / np.abs(Ro).max()
+
+
+@pytest.mark.parametrize("prec", ["bf16tc", "f16tc"])
 @pytest.mark.parametrize("shape", [(1000, 200, 900, 15, 3), (517, 97, 333, 17, 2),
                                    (2048, 300, 1500, 16, 5), (64, 33, 70, 15, 1)])
-def test_sketch_bf16_tensor_core(cmm, shape):
-    # BF16 operands with exact +-1 Hadamard blocks, FP32 accumulation:
-    # error relative to sum_t ||A_t|| ||B_t|| within 2e-2
+def test_sketch_tensor_core(cmm, shape, prec):
+    # 16-bit operands with exact +-1 Hadamard blocks, FP32 accumulation: the
+    # error against the oracle on the same (FP32-rounded) inputs within TC_TOL,
+    # and far below the signal
     m, k, p, L, d = shape
     g = np.random.default_rng(m + k + p)
     A = g.standard_normal((m, k))
     B = g.standard_normal((k, p))
     h = cmm.make_hashes(300 + L, d, L)
-    R = cmm.sketch(_dev(A, torch.float32), _dev(B, torch.float32), h, prec="bf16tc").cpu().numpy()
-    A32 = A.astype(np.float32).astype(np.float64)
-    B32 = B.astype(np.float32).astype(np.float64)
-    Ro = orc.compress(A32, B32, h.params, L, nthreads=8)
-    err = np.abs(R - Ro).max() / _norm_scale(A32, B32)
-    assert err <= 2e-2, err
-    # and it is a real approximation, not noise: the error is far below the signal
-    assert np.abs(R - Ro).max() < 0.05 * np.abs(Ro).max()
+    err_norm, err_max = _tc_error(cmm, A, B, h, L, prec)
+    assert err_norm <= TC_TOL[prec][0], err_norm
+    assert err_max <= TC_TOL[prec][1], err_max
 
 
-def test_sketch_bf16_needs_large_slices(cmm):
+def test_sketch_f16_more_precise_than_bf16(cmm):
+    # same input, same hashes: FP16 operands (3 more significand bits) give a
+    # smaller error than BF16 ones
+    m, k, p, L, d = 1500, 256, 1300, 16, 3
+    g = np.random.default_rng(41)
+    A = g.standard_normal((m, k))
+    B = g.standard_normal((k, p))
+    h = cmm.make_hashes(41, d, L)
+    e16 = _tc_error(cmm, A, B, h, L, "f16tc")[1]
+    ebf = _tc_error(cmm, A, B, h, L, "bf16tc")[1]
+    assert e16 < 0.5 * ebf, (e16, ebf)
+
+
+@pytest.mark.parametrize("prec", ["bf16tc", "f16tc"])
+@pytest.mark.parametrize("L", [15, 16])
+def test_tensor_core_extreme_columns(cmm, prec, L):
+    # the fixed-point scale per column keeps the 16-bit operands in range for
+    # column scales from 1e-20 to 1e15 (FP16: values scaled to below 2^15)
+    m, k, p, d = 1200, 40, 900, 3
+    A, B = _extreme_columns(m, k, p, 11 + L)
+    h = cmm.make_hashes(88 + L, d, L)
+    err_norm, _ = _tc_error(cmm, A, B, h, L, prec)
+    assert err_norm <= TC_TOL[prec][0], err_norm
+
+
+@pytest.mark.parametrize("prec", ["bf16tc", "f16tc"])
+def test_sketch_tensor_core_needs_large_slices(cmm, prec):
     h = cmm.make_hashes(1, 3, 12)
     A = torch.zeros((20, 10), dtype=torch.float32, device="cuda")
     B = torch.zeros((10, 30), dtype=torch.float32, device="cuda")
     with pytest.raises(cmm.CmmError) as ei:
-        cmm.sketch(A, B, h, prec="bf16tc")
+        cmm.sketch(A, B, h, prec=prec)
     assert ei.value.code == cmm.ERR_RANGE
 
 
