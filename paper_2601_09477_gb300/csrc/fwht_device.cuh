@@ -197,6 +197,20 @@ __device__ __forceinline__ void round_load_fixed(const float *base, float (&v)[1
     }
 }
 
+// last-round load of 32-bit values that also zeroes them for the next
+// scatter: one shared-memory exchange per word costs the pipe about what a
+// load does, so the separate clearing pass goes (each word is read by exactly
+// one thread in a round, so nothing else reads it after it is zeroed)
+template <typename T, int L, int LE, int K>
+__device__ __forceinline__ void round_load_clear(T *base, T (&v)[1 << LE]) {
+    static_assert(sizeof(T) == 4, "32-bit words only");
+    using RK = typename FwhtShape<T, L, LE>::template Round<K>;
+    constexpr int E = 1 << LE;
+    int *ib = reinterpret_cast<int *>(base);
+#pragma unroll
+    for (int j = 0; j < E; ++j) v[j] = __int_as_float(atomicExch(ib + RK::addr(0, j), 0));
+}
+
 // Transform the group's slice Sg in place, leaving the result in registers v
 // (round NR-1 layout) and the shared array zeroed for the next scatter.  With
 // FX (FP32 only) the slice holds the integer sums of the fixed-point scatter,
@@ -207,10 +221,15 @@ __device__ __forceinline__ void fwht_rounds(T *Sg, T (&v)[1 << LE], int q, int g
     using S = FwhtShape<T, L, LE>;
     using RK = typename S::template Round<K>;
     constexpr int E = S::E;
+    // FP32 transforms of more than one round zero the slice while the last
+    // round reads it; the others store zeros after the last round
+    constexpr bool kExch = sizeof(T) == 4 && K > 0 && K + 1 == S::NR;
     T *base = Sg + RK::addr(q, 0);
     if constexpr (FX && K == 0) {
         static_assert(sizeof(T) == 4, "fixed-point scatter is FP32 only");
         round_load_fixed<L, LE>(base, v, inv);
+    } else if constexpr (kExch) {
+        round_load_clear<T, L, LE, K>(base, v);
     } else {
         round_load<T, L, LE, K>(base, v);
     }
@@ -219,7 +238,7 @@ __device__ __forceinline__ void fwht_rounds(T *Sg, T (&v)[1 << LE], int q, int g
         round_store<T, L, LE, K>(base, v);
         group_sync<S::P>(g);
         fwht_rounds<T, L, LE, K + 1>(Sg, v, q, g);
-    } else {
+    } else if constexpr (!kExch) {
         T zero[E];
 #pragma unroll
         for (int j = 0; j < E; ++j) zero[j] = T(0);
