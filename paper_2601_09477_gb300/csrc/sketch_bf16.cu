@@ -32,8 +32,9 @@
 // 2^-25 there.
 //
 // Shared memory: the integer slice (2^15 words, element u at word
-// u ^ (((u >> 4) & 3) << 3): pass 1's 64-bit loads of a half-warp hit 32
-// distinct banks; pass 1 clears what it reads), then the BF16 slice between
+// u ^ (((u >> 4) & 3) << 3): pass 1's 64-bit accesses of a half-warp hit 32
+// distinct banks; pass 1 reads and clears each pair of words with one 64-bit
+// exchange), then the BF16 slice between
 // the passes (u at u + 2 * ((u >> 8) + 7 * (u >> 12)); pass-2 loads are
 // bank-conflict free, pass-1 stores 2-way conflicted; fully rewritten by every
 // pass 1, so never cleared).
@@ -220,11 +221,13 @@ __device__ __forceinline__ void bf_fwht(int *Si, uint16_t *S16, const HFrags &f,
         for (int h = 0; h < 2; ++h) {
             const int b = 8 * h + g;
             const int u0 = 2 * c + 16 * b + 256 * tau;
-            int2 *p0 = reinterpret_cast<int2 *>(Si + bf_swz(u0));       // elements u0, u0 + 1
-            int2 *p1 = reinterpret_cast<int2 *>(Si + bf_swz(u0 + 8));   // u0 + 8, u0 + 9
-            const int2 w0 = *p0, w1 = *p1;
-            *p0 = make_int2(0, 0);
-            *p1 = make_int2(0, 0);
+            // elements (u0, u0 + 1) and (u0 + 8, u0 + 9), each pair read and
+            // zeroed for the next scatter by one 64-bit exchange
+            auto *p0 = reinterpret_cast<unsigned long long *>(Si + bf_swz(u0));
+            auto *p1 = reinterpret_cast<unsigned long long *>(Si + bf_swz(u0 + 8));
+            const unsigned long long r0 = atomicExch(p0, 0ull), r1 = atomicExch(p1, 0ull);
+            const int2 w0 = make_int2((int)(uint32_t)r0, (int)(uint32_t)(r0 >> 32));
+            const int2 w1 = make_int2((int)(uint32_t)r1, (int)(uint32_t)(r1 >> 32));
             xb[h][0] = int2_to_16x2<F16>(w0, inv);
             xb[h][1] = int2_to_16x2<F16>(w1, inv);
         }

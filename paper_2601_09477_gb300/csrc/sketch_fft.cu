@@ -255,11 +255,11 @@ __device__ __forceinline__ void fft_slice(float2 *S, const float2 *tlo, const fl
         const int g = q + 256 * jg;
 #pragma unroll
         for (int l = 0; l < 8; ++l) {
-            float2 *p = S + fpad(8 * g + l);
-            const float2 v = *p;
-            re[8 * jg + l] = v.x;
-            im[8 * jg + l] = v.y;
-            *p = make_float2(0.f, 0.f);
+            // read and zeroed for the next scatter by one 64-bit exchange
+            auto *p = reinterpret_cast<unsigned long long *>(S + fpad(8 * g + l));
+            const unsigned long long v = atomicExch(p, 0ull);
+            re[8 * jg + l] = __uint_as_float((uint32_t)v);
+            im[8 * jg + l] = __uint_as_float((uint32_t)(v >> 32));
         }
     }
     dft_dif<8, 0, kFE>(re, im);

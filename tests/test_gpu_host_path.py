@@ -68,18 +68,21 @@ def test_host_path_four_parts_full_size(cmm):
     assert (3, 11) in set(zip(I.tolist(), J.tolist()))
 
 
-def test_host_path_padded_small(cmm):
+@pytest.mark.parametrize("prec,L", [("f32", 12), ("bf16tc", 15), ("f16tc", 15)])
+def test_host_path_padded_small(cmm, prec, L):
     # below the split thresholds: one part, one row block; padded leading
-    # dimensions on the host side
-    m, k, p, L, d = 300, 200, 250, 12, 3
+    # dimensions on the host side; every butterfly precision
+    m, k, p, d = 300, 200, 250, 3
     g = np.random.default_rng(3)
     Abig = torch.from_numpy(g.standard_normal((m, k + 7)).astype(np.float32)).pin_memory()
     Bbig = torch.from_numpy(g.standard_normal((k, p + 3)).astype(np.float32)).pin_memory()
     A, B = Abig[:, :k], Bbig[:, :p]
     h = cmm.make_hashes(5, d, L)
-    Ch, _ = cmm.multiply_host(A, B, h, prec="f32", tau=1e30, capacity=4)
-    Cd = cmm.multiply(A.cuda(), B.cuda(), h, prec="f32")
+    Ch, _ = cmm.multiply_host(A, B, h, prec=prec, tau=1e30, capacity=4)
+    Cd = cmm.multiply(A.cuda(), B.cuda(), h, prec=prec)
     assert torch.equal(Ch, Cd.cpu())
+    if prec != "f32":
+        return
     # and the estimate is the oracle's decompression of the oracle's sketch
     A64 = A.double().numpy()
     B64 = B.double().numpy()
