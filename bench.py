@@ -109,6 +109,27 @@ def alu_roofline(kernel: str, ops: float, ms: float, note: str = "") -> dict:
     return out
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine
+    type), for the CPU baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine() or "unknown"
+
+
 def timed_oracle(fn) -> float:
     """Seconds one call of an oracle function takes on the host cores."""
     t0 = time.perf_counter()
@@ -442,9 +463,17 @@ def run_cmm(a):
         threads = orc.max_threads()
         # the whole step at the benchmark size takes the oracle about 5 s on 16 cores
         cpu_ms, sample, secs = oracle_sample(A_np, B_np, h.params, L, n, d, tau, n, n, threads)
+        # the same oracle on one core, on a sample (Compress over n/64 inner
+        # indices, Decompress of n/256 rows) scaled to the whole step
+        one_ms, one_sample, one_secs = oracle_sample(A_np, B_np, h.params, L, n, d, tau,
+                                                     max(16, n // 64), max(16, n // 256), 1)
         result["cpu_baseline"] = {"value": round(cpu_ms, 1), "unit": "ms", "cores": threads,
                                   "kind": "oracle", "sample": sample,
-                                  "sample_seconds": round(secs, 2)}
+                                  "sample_seconds": round(secs, 2), "cpu_model": cpu_model(),
+                                  "host_cpus": os.cpu_count(),
+                                  "one_core": {"value": round(one_ms, 1), "unit": "ms",
+                                               "sample": one_sample,
+                                               "sample_seconds": round(one_secs, 2)}}
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
