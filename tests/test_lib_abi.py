@@ -126,3 +126,21 @@ def test_parameter_rule_and_categories():
     assert ev.category(sat, n) == "satisfactory"
     none = dict(sat, **{"B_ge_0.5": 5})
     assert ev.category(none, n) == "none"
+
+
+def test_tensor_core_precisions_checked_before_launch(cmm):
+    # BF16TC and FP16TC share the 2^15-slice plan: the same workspace, and a
+    # sketch length below one slice is refused before anything is launched
+    lib = cmm.lib
+    ws_bf = lib.cmm_sketch_workspace_bytes(512, 300, 400, 3, 16, cmm.F32, cmm.PREC_BF16TC, 0)
+    ws_f16 = lib.cmm_sketch_workspace_bytes(512, 300, 400, 3, 16, cmm.F32, cmm.PREC_F16TC, 0)
+    assert ws_bf > 0 and ws_bf == ws_f16
+    params = np.zeros((3, 8), dtype=np.uint64)
+    small = cmm.Hashes(3, 12, params)
+    dummy = ctypes.c_void_p(256)   # never dereferenced: the calls fail their checks
+    for prec in (cmm.PREC_BF16TC, cmm.PREC_F16TC):
+        assert lib.cmm_sketch(dummy, 4, 0, dummy, 4, cmm.F32, 4, 4, 4, small.ref, prec,
+                              dummy, dummy, 1 << 30, None) == cmm.ERR_RANGE
+        assert "tensor-core" in lib.cmm_last_error().decode()
+    assert lib.cmm_sketch(dummy, 4, 0, dummy, 4, cmm.F32, 4, 4, 4, small.ref, 4,
+                          dummy, dummy, 1 << 30, None) == cmm.ERR_ARG
