@@ -64,13 +64,19 @@ def parse():
     return ap.parse_args()
 
 
+L2_BYTES = 129e6   # L2 of one GB300
+
+
 def workload_config(a):
+    ab = 2 * a.n * a.n * 8
+    l2 = ("inputs (%.0f MiB) larger than L2 (129 MB)" % (ab / 2**20) if ab > L2_BYTES else
+          "inputs (%.0f MiB) fit in L2 (129 MB); L2 not flushed between steps" % (ab / 2**20))
     return {
         "workload": "planted +-1 correlations n=%d (64 row pairs, rho=0.9, B=A^T, FP64 storage), "
                     "b=2^%d, d=%d, median, heavy hitters |C|>=n/2" % (a.n, a.log2b, a.d),
         "n": a.n, "m": a.n, "k": a.n, "p": a.n, "log2b": a.log2b, "d": a.d,
-        "tau": a.n / 2, "input_dtype": "f64", "l2": "inputs (%.0f MiB) larger than L2" %
-        (2 * a.n * a.n * 8 / 2**20), "parallelism": "replicas (one problem per GPU)",
+        "tau": a.n / 2, "input_dtype": "f64", "l2": l2,
+        "parallelism": "replicas (one problem per GPU)",
     }
 
 
