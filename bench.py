@@ -67,10 +67,15 @@ def parse():
 L2_BYTES = 129e6   # L2 of one GB300
 
 
+def l2_note(nbytes: float) -> str:
+    """How the timed steps relate to the L2: inputs larger than it, or not."""
+    if nbytes > L2_BYTES:
+        return "inputs (%.0f MiB) larger than L2 (129 MB)" % (nbytes / 2**20)
+    return "inputs (%.0f MiB) fit in L2 (129 MB); L2 not flushed between steps" % (nbytes / 2**20)
+
+
 def workload_config(a):
-    ab = 2 * a.n * a.n * 8
-    l2 = ("inputs (%.0f MiB) larger than L2 (129 MB)" % (ab / 2**20) if ab > L2_BYTES else
-          "inputs (%.0f MiB) fit in L2 (129 MB); L2 not flushed between steps" % (ab / 2**20))
+    l2 = l2_note(2 * a.n * a.n * 8)
     return {
         "workload": "planted +-1 correlations n=%d (64 row pairs, rho=0.9, B=A^T, FP64 storage), "
                     "b=2^%d, d=%d, median, heavy hitters |C|>=n/2" % (a.n, a.log2b, a.d),
@@ -547,7 +552,8 @@ def run_batched(a):
            "value": best, "unit": "ms", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
            "higher_is_better": False, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "256 problems, m,k,p uniform in [512,4096], b=2^10..2^15, d=5, "
-                                  "16 planted spikes each, FP32, A given as A^T"},
+                                  "16 planted spikes each, FP32, A given as A^T",
+                      "l2": l2_note(sum(At.numel() + B.numel() for (At, B, _, _) in raw) * 4)},
            "alu_tops": round(flops / (best * 1e-3) / 1e12, 3), "entries_estimated": outputs,
            "gpu_launches_per_step": 1}
     res.update(out)
@@ -626,7 +632,8 @@ def run_precision(a):
            "value": times["bf16tc"], "unit": "ms", "n_gpus": 1, "steps": a.steps,
            "warmup": a.warmup, "higher_is_better": False, "dtype": "bf16tc", "data": "synthetic",
            "config": {"workload": "n=16384, A=Q orthogonal, B=Q^T S + 1e-3 noise, 1024 entries "
-                                  "N(0,1)*100, b=2^18, d=7, FP32 storage"},
+                                  "N(0,1)*100, b=2^18, d=7, FP32 storage",
+                      "l2": l2_note(2 * n * n * 4)},
            "ms": times, "R_err_rel_to_sum_norms": err,
            "R_err_rel_to_rms": {p: float((Rs[p] - Rs["f64"]).abs().max().item() / rms)
                                 for p in low},
@@ -696,7 +703,7 @@ def run_diff(a):
            "value": round(fb_ms, 3), "unit": "ms", "n_gpus": 1, "steps": a.steps,
            "warmup": a.warmup, "higher_is_better": False, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "n=4096 FP32, N(0,1)/sqrt(n) + 256 spikes, b=2^14, d=5, "
-                                  "loss over 4096 weighted pairs"},
+                                  "loss over 4096 weighted pairs", "l2": l2_note(2 * 4096 * 4096 * 4)},
            "forward_ms": round(f_ms, 3), "forward_backward_ms": round(fb_ms, 3),
            "kernels_ms_per_step": kernels, "clocks": clk,
            "roofline": alu_roofline("adjoint_f32", adj_ops, kernels.get("adjoint_f32", float("nan")),
@@ -760,7 +767,7 @@ def run_cyclic(a):
            "steps": a.steps, "warmup": a.warmup, "higher_is_better": False, "dtype": "f32",
            "data": "synthetic",
            "config": {"workload": "planted +-1 correlations n=%d (64 pairs, rho=0.9, B=A^T, FP32 "
-                                  "storage), b=2^%d, d=%d" % (n, L, d)},
+                                  "storage), b=2^%d, d=%d" % (n, L, d), "l2": l2_note(2 * n * n * 4)},
            "ms": times, "fft_over_fwht": round(times["cyclic"] / times["fwht"], 2),
            "kernels_ms_per_step": kernels, "planted_recall": recall, "clocks": clocks.stop(),
            "roofline": alu_roofline("sketch_cyclic", d * n * (5.0 * (1 << L) * L + 4.0 * (1 << L)),
@@ -822,7 +829,7 @@ def run_instances(a):
            "unit": "ms", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
            "higher_is_better": False, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "Logunit, Diagonal, Covariance, Lightbulb generators, n=4096, "
-                                  "FP64 storage"}, "rows": rows}
+                                  "FP64 storage", "l2": l2_note(2 * 4096 * 4096 * 8)}, "rows": rows}
     if not a.no_cpu:
         # the oracle on the first row's instance: Compress over ks of the n inner
         # indices and Decompress of `nr` rows, scaled linearly to one multiply
@@ -903,7 +910,8 @@ def run_paper(a):
            "value": rows[-1]["f32_s"], "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 1,
            "higher_is_better": False, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "sizes of the paper's Table 7 rows up to n=2^16, N(0,1) FP64 "
-                                  "operands, d and b from the paper's parameter rule"},
+                                  "operands, d and b from the paper's parameter rule",
+                      "l2": l2_note(2 * 2**15 * 2**15 * 8)},
            "rows": rows}
     print(json.dumps(res), flush=True)
     return 0
