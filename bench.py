@@ -507,7 +507,8 @@ def _events_ms(fn, reps):
 
 def run_batched(a):
     """256 uneven problems in one persistent launch, replayed from a CUDA graph;
-    default tiles vs autotuned tiles."""
+    default tiles vs autotuned tiles; against the same problems run one call at
+    a time (FP32 butterflies and the plain FP64 form)."""
     import torch
     from paper_2601_09477_gb300 import autotune, cmm
     from paper_2601_09477_gb300 import workloads as wl
@@ -545,6 +546,36 @@ def run_batched(a):
     out["roofline"] = alu_roofline("batched_kernel", flops, best,
                                    "per problem d*k*(2 b log2 b + b): butterflies of both "
                                    "sketches and the MAC")
+    # the same problems one call at a time through cmm_multiply, with FP32
+    # butterflies and in the plain FP64 form, and the batched sketch's error
+    # against the FP64 one (relative to sum_t ||A_t|| ||B_t|| of each problem)
+    Rb = [pb.R.clone() for pb in probs]
+    R64 = [torch.empty((d, pb.hashes.b), dtype=torch.float64, device="cuda") for pb in probs]
+    wsq = torch.empty(max(cmm.multiply_workspace_bytes(pb.At.shape[1], pb.At.shape[0],
+                                                       pb.B.shape[1], pb.hashes, torch.float32,
+                                                       pr, transA=True)
+                          for pb in probs for pr in ("f32", "f64")),
+                      dtype=torch.uint8, device="cuda")
+
+    def one_by_one(prec, Rs=None):
+        for q, pb in enumerate(probs):
+            cmm.multiply(pb.At, pb.B, pb.hashes, prec=prec, transA=True, out=pb.C, ws=wsq,
+                         R=Rs[q] if Rs is not None else None)
+
+    one_by_one("f32")
+    torch.cuda.synchronize()
+    seq32 = _events_ms(lambda: one_by_one("f32"), 1)
+    seq64 = _events_ms(lambda: one_by_one("f64", R64), 1)
+    err = 0.0
+    for q, pb in enumerate(probs):
+        sc = float((torch.linalg.vector_norm(pb.At.double(), dim=1) *
+                    torch.linalg.vector_norm(pb.B.double(), dim=1)).sum().item())
+        err = max(err, float((Rb[q] - R64[q]).abs().max().item()) / max(sc, 1e-300))
+    out["one_call_per_problem_ms"] = {"f32": round(seq32, 3), "f64": round(seq64, 3)}
+    out["speedup_vs_one_call_per_problem"] = {"f32": round(seq32 / best, 2),
+                                              "f64": round(seq64 / best, 2)}
+    out["R_err_vs_fp64_rel_to_sum_norms"] = err
+    del Rb, R64, wsq
     if not a.no_cpu:
         out["cpu_baseline"] = batched_oracle(raw, probs, d, nsample=32)
     res = {"metric": "batched: 256 uneven problems (sketch + FP64 finish + median extraction), "
