@@ -325,12 +325,18 @@ def run_cmm(a):
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    # one event per step boundary as well (the paper reports min and median)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps - 1)]
     w0 = time.perf_counter()
     e0.record(stream)
-    for _ in range(a.steps):
+    for it in range(a.steps):
         I, J, V = step(a.prec)
+        if it + 1 < a.steps:
+            marks[it].record(stream)
     e1.record(stream)
     torch.cuda.synchronize()
+    bounds = [e0] + marks + [e1]
+    per_step = sorted(bounds[q].elapsed_time(bounds[q + 1]) for q in range(a.steps))
     wall = time.perf_counter() - w0
     barrier()
     cmm.trace_enable(False)
@@ -386,7 +392,9 @@ def run_cmm(a):
                                                      for k, v in sorted(trace.items())},
               "heavy_hitters": {"count": int(len(Ih)), "offdiag": offdiag,
                                 "planted_recall": recall},
-              "wall_s_timed": round(wall, 3)}
+              "wall_s_timed": round(wall, 3),
+              "step_ms_min": round(per_step[0], 4),
+              "step_ms_median": round(per_step[len(per_step) // 2], 4)}
 
     # plain FP64 form on the same input: time and R agreement
     if not a.no_fp64 and a.prec != "f64":
