@@ -191,9 +191,11 @@ def diff_problem(n: int = 4096, spikes: int = 256, pairs: int = 4096, seed: int 
 # ---- the paper's instance families (Sec. 5.2) ----------------------------------
 
 def logunit(n: int, seed: int = 2001):
-    """C = D P: log2 n entries equal to 1, the rest 0.001, one per row/column.
-    A = D1 A~, B = A~^{-1} D2 P with floor(log2 n / 2) (resp. ceil) entries 100
-    and the rest 0.01 on D1 (resp. D2, on disjoint positions).  (The paper
+    """C = D P: log2 n entries equal to 1, the rest 0.01 * 0.01 = 1e-4, one per
+    row/column.  A = D1 A~, B = A~^{-1} D2 P with floor(log2 n / 2) (resp. ceil)
+    entries 100 and the rest 0.01 on D1 (resp. D2, on disjoint positions).  (The
+    paper's text calls the small entries 0.001; its construction, followed here,
+    makes them 1e-4.)  (The paper
     writes A = A~ D1 but derives A B = D1 A~ A~^{-1} D2 P = D1 D2 P, which needs
     D1 on the left.)"""
     g = rng(seed)
