@@ -105,3 +105,15 @@ def test_covariance_planted_correlation():
     assert abs(C[i, j] - rho) < 0.15
     C[i, j] = 0.0
     assert np.abs(C).max() < 0.3
+
+
+def test_correctness_counters_by_hand():
+    # the counters of Sec. 5.3 on a 2 x 3 example counted by hand
+    import torch
+    from paper_2601_09477_gb300 import evaluate as ev
+    C_true = torch.tensor([[1.0, 0.0, 0.001], [0.0, -0.8, 0.0]], dtype=torch.float64)
+    big = C_true.abs() >= 0.5
+    C_hat = torch.tensor([[0.95, 0.6, 0.0], [0.2, -0.45, 0.05]], dtype=torch.float64)
+    c = ev.counters(C_hat, big, C_true)
+    assert c == {"big": 2, "small": 4, "B_ge_0.5": 1, "S_le_0.5": 3,
+                 "B_eps_le_0.1": 1, "S_eps_le_0.1": 2}
