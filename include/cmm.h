@@ -116,7 +116,9 @@ int cmm_sketch(const void *A, int64_t lda, int32_t transA, const void *B, int64_
  * cmm_sketch_workspace_bytes exceeds that size is rejected with CMM_ERR_RANGE
  * before anything runs.  The first call on each device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  All calls share the array, so calls
+ * first call before any stream capture.  The address is kept for the life of
+ * the process: after a cudaDeviceReset of that device it is no longer valid,
+ * so do not call this function again in that process.  All calls share the array, so calls
  * that overlap on the GPU race and must be serialised by the caller.  The
  * function calls no cudaMalloc/cudaFree or other allocating routine. */
 int cmm_sketch_noalloc(const void *A, int64_t lda, int32_t transA, const void *B, int64_t ldb,
