@@ -115,12 +115,13 @@ int cmm_sketch(const void *A, int64_t lda, int32_t transA, const void *B, int64_
  * every GPU that loads the library until the process exits.  A problem whose
  * cmm_sketch_workspace_bytes exceeds that size is rejected with CMM_ERR_RANGE
  * before anything runs.  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  The address is kept for the life of
- * the process: after a cudaDeviceReset of that device it is no longer valid,
- * so do not call this function again in that process.  All calls share the array, so calls
- * that overlap on the GPU race and must be serialised by the caller.  The
- * function calls no cudaMalloc/cudaFree or other allocating routine. */
+ * device address (cudaGetSymbolAddress) with that device current and keeps it
+ * for the CUDA context it was found in; a call in another context, or after a
+ * cudaDeviceReset, finds a new context id and looks the address up again.
+ * Make the first call on each device (and the first after a reset) before any
+ * stream capture.  All calls share the array, so calls that overlap on the GPU
+ * race and must be serialised by the caller.  The function calls no
+ * cudaMalloc/cudaFree or other allocating routine. */
 int cmm_sketch_noalloc(const void *A, int64_t lda, int32_t transA, const void *B, int64_t ldb,
                        int32_t dtype, int64_t m, int64_t k, int64_t p, const cmm_hashes *hs,
                        int32_t prec, double *R, void *stream);

@@ -194,20 +194,36 @@ def extract(R: np.ndarray, hp: np.ndarray, m: int, p: int, reduce: int = MEDIAN,
 
 
 def heavy_hitters(R: np.ndarray, hp: np.ndarray, m: int, p: int, tau: float,
-                  reduce: int = MEDIAN, rows=None, capacity: int = 1 << 20):
-    """(I, J, V) of all |estimate| >= tau, sorted by (i, j)."""
+                  reduce: int = MEDIAN, rows=None, capacity: int = 1 << 20,
+                  nthreads: int = 1):
+    """(I, J, V) of all |estimate| >= tau, sorted by (i, j).
+
+    With ``nthreads`` > 1 the rows are split into contiguous ranges, each
+    listed by the same C routine on its own host thread, and the lists are
+    joined in row order (the per-entry arithmetic is unchanged)."""
     R = _f64(R)
     hp = np.ascontiguousarray(hp, dtype=np.uint64)
     L = int(R.shape[1]).bit_length() - 1
     i0, i1 = rows if rows is not None else (0, m)
-    I = np.zeros(capacity, dtype=np.int32)
-    J = np.zeros(capacity, dtype=np.int32)
-    V = np.zeros(capacity, dtype=np.float64)
-    n = _load().orc_heavy_hitters(_ptr(R), _ptr(hp), hp.shape[0], L, i0, i1, p, reduce,
-                                  float(tau), _ptr(I), _ptr(J), _ptr(V), capacity)
-    if n > capacity:
-        raise ValueError("heavy-hitter capacity %d too small for %d entries" % (capacity, n))
-    return I[:n].copy(), J[:n].copy(), V[:n].copy()
+
+    def one(a: int, b: int):
+        I = np.zeros(capacity, dtype=np.int32)
+        J = np.zeros(capacity, dtype=np.int32)
+        V = np.zeros(capacity, dtype=np.float64)
+        n = _load().orc_heavy_hitters(_ptr(R), _ptr(hp), hp.shape[0], L, a, b, p, reduce,
+                                      float(tau), _ptr(I), _ptr(J), _ptr(V), capacity)
+        if n > capacity:
+            raise ValueError("heavy-hitter capacity %d too small for %d entries" % (capacity, n))
+        return I[:n].copy(), J[:n].copy(), V[:n].copy()
+
+    nthreads = max(1, min(int(nthreads), i1 - i0))
+    if nthreads == 1:
+        return one(i0, i1)
+    from concurrent.futures import ThreadPoolExecutor
+    cuts = [i0 + (i1 - i0) * q // nthreads for q in range(nthreads + 1)]
+    with ThreadPoolExecutor(max_workers=nthreads) as ex:   # ctypes releases the GIL
+        parts = list(ex.map(lambda q: one(cuts[q], cuts[q + 1]), range(nthreads)))
+    return tuple(np.concatenate([pt[c] for pt in parts]) for c in range(3))
 
 
 def mean_at_pairs(R: np.ndarray, hp: np.ndarray, I, J) -> np.ndarray:

@@ -3,6 +3,7 @@
 // heavy-hitter drivers.  No function here allocates device memory; every
 // scratch byte comes from the caller's workspace.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -51,17 +52,25 @@ cudaEvent_t tr_event() {
     return e;
 }
 
+// SM count of the current device, cached per device index (the plans size
+// grids by it, so a process with GPUs of different sizes plans each for its own)
 int num_sms() {
-    static int cached = 0;
-    if (cached) return cached;
+    constexpr int kDevs = 64;
+    static std::atomic<int> cached[kDevs];
     int dev = 0, n = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0) {
-        cached = n;
-    } else {
+    if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();   // no device here: plan for a GB300
-        n = 152;
+        return 152;
     }
+    if (dev >= 0 && dev < kDevs) {
+        const int c = cached[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        return 152;
+    }
+    if (dev >= 0 && dev < kDevs) cached[dev].store(n, std::memory_order_relaxed);
     return n;
 }
 

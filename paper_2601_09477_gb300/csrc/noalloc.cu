@@ -27,11 +27,50 @@ namespace {
 
 constexpr int kMaxDevices = 256;
 std::mutex g_mu;
-void *g_scratch[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device.  In host code the array's name is only a host-side stand-in; a
-// kernel must get the address cudaGetSymbolAddress returns.
+// One cached lookup per device: the array's device address and the id of the
+// context it was looked up in.  Context ids are never reused within a process,
+// so after a cudaDeviceReset (which destroys the primary context) or under
+// another context on the same device the id differs and the lookup runs again.
+struct Cached {
+    void *addr = nullptr;
+    unsigned long long ctx_id = 0;
+    bool valid = false;
+};
+Cached g_cache[kMaxDevices];
+
+// driver entry points reached through the runtime (no link-time libcuda)
+typedef int (*ctx_get_current_fn)(void **);
+typedef int (*ctx_get_id_fn)(void *, unsigned long long *);
+
+// id of the calling thread's current context; false when it cannot be read
+// (then the address is looked up again on every call)
+bool current_context_id(unsigned long long *id) {
+    static ctx_get_current_fn get_current = nullptr;
+    static ctx_get_id_fn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<ctx_get_current_fn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<ctx_get_id_fn>(f);
+        cudaGetLastError();
+    });
+    if (!get_current || !get_id) return false;
+    void *ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx) return false;
+    return get_id(ctx, id) == 0;
+}
+
+// Device address of the scratch array in the current device's context.  In
+// host code the array's name is only a host-side stand-in; a kernel must get
+// the address cudaGetSymbolAddress returns.  It is looked up with the device
+// current on the first call in each context and kept for that context.
 int scratch_on_current_device(void **out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -42,19 +81,33 @@ int scratch_on_current_device(void **out) {
     }
     if (dev < 0 || dev >= kMaxDevices)
         return cmm::set_error(CMM_ERR_RANGE, "cmm_sketch_noalloc: device index out of range");
+    // initialises the device's primary context if no context is current yet
+    // (so that the id below names the context the lookup and the launches use)
+    e = cudaSetDevice(dev);
+    if (e != cudaSuccess) {
+        char msg[256];
+        std::snprintf(msg, sizeof msg, "cmm_sketch_noalloc: context set-up: %s", cudaGetErrorString(e));
+        return cmm::set_error(CMM_ERR_CUDA, msg);
+    }
+    unsigned long long id = 0;
+    const bool have_id = current_context_id(&id);
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch[dev]) {
+    Cached &c = g_cache[dev];
+    if (!(have_id && c.valid && c.ctx_id == id)) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_sketch_noalloc_scratch);
         if (e != cudaSuccess || !p) {
             char msg[256];
             std::snprintf(msg, sizeof msg, "cmm_sketch_noalloc: cudaGetSymbolAddress: %s",
                           cudaGetErrorString(e));
+            c.valid = false;
             return cmm::set_error(CMM_ERR_CUDA, msg);
         }
-        g_scratch[dev] = p;
+        c.addr = p;
+        c.ctx_id = id;
+        c.valid = have_id;
     }
-    *out = g_scratch[dev];
+    *out = c.addr;
     return CMM_OK;
 }
 

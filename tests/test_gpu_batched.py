@@ -133,7 +133,7 @@ def test_batched_rejects_bad_problems(cmm):
 
 def test_batched_256_uneven_problems(cmm):
     # 256 problems, m, k, p uniform in [512, 4096], b = 2^10 .. 2^15, d = 5, FP32,
-    # 16 planted spikes each; sampled problems checked against the oracle
+    # 16 planted spikes each; one problem per sketch length checked in full
     d = 5
     raw = wl.batch_problems_device(count=256, seed=1004, device="cuda")
     probs = [cmm.Problem(At, B, cmm.make_hashes(7000 + q, d, L)) for q, (At, B, L, _) in enumerate(raw)]
@@ -141,18 +141,22 @@ def test_batched_256_uneven_problems(cmm):
     batch.launch()
     assert batch.status() == cmm.OK
     work = [pb.At.shape[0] * (1 << pb.hashes.log2b) * pb.hashes.log2b for pb in probs]
-    order = np.argsort(work)
-    # the two cheapest problems in full, plus the largest-b problem on sampled rows
-    for q in list(order[:2]):
+    # the cheapest problem of every sketch length b = 2^10 .. 2^15 in full: the
+    # whole R against the oracle's Compress, the whole estimate against the
+    # oracle's Decompress of the same R
+    classes = sorted({pb.hashes.log2b for pb in probs})
+    assert classes == list(range(10, 16))
+    for L in classes:
+        q = min((q for q in range(len(probs)) if probs[q].hashes.log2b == L), key=lambda q: work[q])
         pb = probs[q]
         A = pb.At.double().cpu().numpy().T.copy()
         B = pb.B.double().cpu().numpy()
-        L = pb.hashes.log2b
-        Ro = orc.compress(A, B, pb.hashes.params, L, nthreads=16)
+        Ro = orc.compress(A, B, pb.hashes.params, L, nthreads=orc.max_threads())
         R = pb.R.cpu().numpy()
-        assert np.abs(R - Ro).max() <= 1e-5 * _scale(A, B)
-        Co = orc.extract(R, pb.hashes.params, A.shape[0], B.shape[1])
-        assert np.array_equal(pb.C.cpu().numpy(), Co)
+        assert np.abs(R - Ro).max() <= 1e-5 * _scale(A, B), (q, L)
+        Co = orc.extract(R, pb.hashes.params, A.shape[0], B.shape[1], nthreads=8)
+        assert np.array_equal(pb.C.cpu().numpy(), Co), (q, L)
+    # the largest-b, largest-m problem on sampled entries and rows
     qb = int(np.argmax([pb.hashes.log2b * 10**8 + pb.At.shape[0] for pb in probs]))
     pb = probs[qb]
     A = pb.At.double().cpu().numpy().T.copy()

@@ -42,3 +42,34 @@ def test_variance_experiment(name, log2b):
     mean, var, true, bound = evaluate.variance_experiment(name, 1024, log2b, draws)
     assert abs(mean - true) <= 5.0 * (bound / draws) ** 0.5
     assert var <= 1.25 * bound
+
+
+@pytest.mark.parametrize("name,c_d,c_b", [("logunit", 1.0, 0.5), ("diagonal", 2.0, 4.0),
+                                          ("covariance", 1.5, 4.0), ("lightbulb", 2.0, 4.0)])
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_instance_matches_oracle(name, c_d, c_b, prec, tol):
+    # the paper's four families at n = 1024 with Table 3's parameters: the whole
+    # R against the oracle's Compress on the same operands (Logunit's 1e-4
+    # entries beside 1 and Diagonal's A^-1 exercise the fixed-point scatter's
+    # per-column scale), the whole estimate against the oracle's Decompress of
+    # the same R, and the category the parameters were chosen for
+    import numpy as np
+    from oracle import oracle as orc
+    from paper_2601_09477_gb300 import cmm, evaluate
+    target = {"logunit": "perfect", "diagonal": "good", "covariance": "satisfactory",
+              "lightbulb": "satisfactory"}[name]
+    n = 1024
+    d, L = evaluate.params(n, c_d, c_b)
+    A, B, Ctrue, big = evaluate.instance(name, n, 5)
+    h = cmm.make_hashes(300, d, L)
+    R = torch.empty((d, 1 << L), dtype=torch.float64, device="cuda")
+    C = cmm.multiply(A, B, h, prec=prec, R=R)
+    An, Bn = A.cpu().numpy(), B.cpu().numpy()
+    Ro = orc.compress(An, Bn, h.params, L, nthreads=orc.max_threads())
+    scale = float(np.sum(np.linalg.norm(An, axis=0) * np.linalg.norm(Bn, axis=1)))
+    Rn = R.cpu().numpy()
+    assert np.abs(Rn - Ro).max() <= tol * scale, (name, prec, np.abs(Rn - Ro).max() / scale)
+    Co = orc.extract(Rn, h.params, n, n, nthreads=8)
+    assert np.array_equal(C.cpu().numpy(), Co)
+    res = evaluate.counters(C, big, Ctrue)
+    assert RANK[evaluate.category(res, n)] >= RANK[target], res

@@ -5,8 +5,8 @@ whose host application owns every allocation, and latency-critical paths that
 cannot pay for cudaMalloc's implicit synchronisation cannot pass a workspace.
 This entry point keeps its scratch in a static device array inside libcmm.
 These checks call it through the C ABI and compare it with cmm_sketch (the
-workspace version) on two calls in a row, so the second call runs on scratch
-that still holds the first call's data.  The file is collected last on purpose.
+workspace version) and with the FP64 oracle on two calls in a row, so the
+second call runs on scratch that still holds the first call's data.  The file is collected last on purpose.
 """
 import ctypes
 
@@ -49,6 +49,7 @@ def _scale(A, B):
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_noalloc_matches_workspace_version_twice(cmm, prec):
+    from oracle import oracle as orc
     g = np.random.default_rng(12)
     problems = [(256, 256, 256, 12, 5, torch.float64, False),
                 (300, 517, 200, 13, 3, torch.float32, True)]
@@ -60,17 +61,35 @@ def test_noalloc_matches_workspace_version_twice(cmm, prec):
         R_na = _noalloc(cmm, A, B, h, prec, transA)
         assert not torch.isnan(R_na).any()
         At = A.t() if transA else A
-        err = (R_na - R_ws).abs().max().item() / _scale(At, B)
+        scale = _scale(At, B)
+        err = (R_na - R_ws).abs().max().item() / scale
         assert err <= TOL[prec], err
+        # and against the FP64 oracle on the same (widened) operand values
+        Ro = orc.compress(A.double().cpu().numpy(), B.double().cpu().numpy(), h.params, L,
+                          transA=transA)
+        err_o = float(np.abs(R_na.cpu().numpy() - Ro).max()) / scale
+        assert err_o <= TOL[prec], err_o
 
 
 def test_noalloc_rejects_oversized_problem(cmm):
-    # n = 8192, b = 2^16, d = 9 needs far more than the static array holds
-    h = cmm.make_hashes(1, 9, 16)
-    need = cmm.lib.cmm_sketch_workspace_bytes(8192, 8192, 8192, 9, 16, cmm.F64, cmm.PREC_F32, 0)
-    assert need > (64 << 20)
-    dummy = ctypes.c_void_p(256)   # never touched: the call fails its size check first
-    rc = cmm.lib.cmm_sketch_noalloc(dummy, 8192, 0, dummy, 8192, cmm.F64, 8192, 8192, 8192,
-                                    h.ref, cmm.PREC_F32, dummy, None)
+    # m = k = p = 64 with b = 2^20 and d = 9: the operands are small, but the
+    # per-block partial sums and the reduced sums (d x b FP64 each) need more
+    # scratch than the static array holds.  Every buffer is real and sized for
+    # the problem, so even a call that got past the size check would only
+    # compute a result.
+    m = k = p = 64
+    L, d = 20, 9
+    h = cmm.make_hashes(1, d, L)
+    need = cmm.lib.cmm_sketch_workspace_bytes(m, k, p, d, L, cmm.F64, cmm.PREC_F32, 0)
+    assert need > (64 << 20)   # CMM_SKETCH_NOALLOC_SCRATCH_BYTES
+    g = np.random.default_rng(5)
+    A = torch.from_numpy(g.standard_normal((m, k))).cuda()
+    B = torch.from_numpy(g.standard_normal((k, p))).cuda()
+    R = torch.zeros((d, 1 << L), dtype=torch.float64, device="cuda")
+    rc = cmm.lib.cmm_sketch_noalloc(A.data_ptr(), k, 0, B.data_ptr(), p, cmm.F64, m, k, p,
+                                    h.ref, cmm.PREC_F32, R.data_ptr(),
+                                    torch.cuda.current_stream().cuda_stream)
     assert rc == cmm.ERR_RANGE
     assert "static array" in cmm.lib.cmm_last_error().decode()
+    torch.cuda.synchronize()
+    assert not R.any()   # nothing ran
