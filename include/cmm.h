@@ -63,7 +63,12 @@ typedef enum {
     CMM_PREC_F64 = 0,     /* FP64 butterflies and accumulation ("plain FP64") */
     CMM_PREC_F32 = 1,     /* FP32 butterflies, FP32 accumulation within a block of t */
     CMM_PREC_BF16TC = 2,  /* BF16 operands with exact +-1 Hadamard blocks on the tensor cores, FP32 accumulation */
-    CMM_PREC_F16TC = 3    /* as BF16TC with FP16 operands, scaled to a fixed range (3 more significand bits) */
+    CMM_PREC_F16TC = 3,   /* as BF16TC with FP16 operands, scaled to a fixed range (3 more significand bits) */
+    CMM_PREC_FX64 = 4     /* exact 64-bit fixed-point butterflies: each column quantised once to integers
+                           * with sum |q| < 2^62 (per-column power of two from its l1 norm), scatter and
+                           * transforms exact in int64, float-float multiply-accumulate; R within the
+                           * FP64 tolerance (quantisation <= 2^-61 |column|_1 per value).  Operands must
+                           * be finite. */
 } cmm_prec;
 
 /* how the d repetitions are combined */

@@ -119,20 +119,24 @@ bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int p
     pl = SketchPlan{};
     pl.prec = prec;
     pl.L = L;
-    const bool f64 = prec == CMM_PREC_F64;
+    const bool fx = prec == CMM_PREC_FX64;   // exact fixed point: FP64 operands, int64 copies
+    const bool f64 = prec == CMM_PREC_F64 || fx;
     const bool bf16 = prec_tc(prec);
     if (bf16 && L < sketch_bf16_llo()) return false;
-    const int maxLlo = bf16 ? sketch_bf16_llo() : (f64 ? kMaxLloF64 : kMaxLloF32);
+    const int maxLlo = bf16 ? sketch_bf16_llo()
+                            : fx ? kMaxLloFx64 : (f64 ? kMaxLloF64 : kMaxLloF32);
     pl.Llo = std::min(L, maxLlo);
     pl.C = 1 << (L - pl.Llo);
     pl.tmem = sketch_tm_supported(prec, pl.Llo) && use_tmem_kernel();
     pl.threads = bf16 ? sketch_bf16_threads()
-                      : pl.tmem ? sketch_tm_threads()
-                                : (f64 ? sketch_threads_f64(pl.Llo) : sketch_threads_f32(pl.Llo));
+                 : fx ? sketch_fx64_threads()
+                 : pl.tmem ? sketch_tm_threads()
+                           : (f64 ? sketch_threads_f64(pl.Llo) : sketch_threads_f32(pl.Llo));
     pl.smem = bf16 ? sketch_bf16_smem()
-                   : pl.tmem ? sketch_tm_smem()
-                             : (f64 ? sketch_smem_f64(pl.Llo) : sketch_smem_f32(pl.Llo));
-    const int LE = bf16 ? pl.Llo : pl.tmem ? 7 : std::min(pl.Llo, f64 ? 4 : 5);
+              : fx ? sketch_fx64_smem(pl.Llo)
+              : pl.tmem ? sketch_tm_smem()
+                        : (f64 ? sketch_smem_f64(pl.Llo) : sketch_smem_f32(pl.Llo));
+    const int LE = bf16 ? pl.Llo : pl.tmem ? 7 : std::min(pl.Llo, (f64 && !fx) ? 4 : 5);
     const int P = (1 << pl.Llo) >> LE;
     const int G = bf16 ? 1 : pl.threads / P;
     const int per_sm = bf16 ? 1 : (pl.tmem || pl.threads < 512) ? 2 : 1;
@@ -199,7 +203,13 @@ bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int p
     pl.off_tab = off;
     off += align_up((size_t)d * pl.C * (m + p) * sizeof(tab_t));
     pl.off_colmax = off;
-    if (prec != CMM_PREC_F64) off += align_up((size_t)2 * k * sizeof(float));
+    if (!f64) off += align_up((size_t)2 * k * sizeof(float));
+    pl.off_Aq = off;
+    if (fx) off += align_up((size_t)k * m * sizeof(long long));
+    pl.off_Bq = off;
+    if (fx) off += align_up((size_t)k * p * sizeof(long long));
+    pl.off_exp = off;
+    if (fx) off += align_up((size_t)2 * k * sizeof(int));
     pl.total = off;
     return true;
 }
@@ -219,7 +229,7 @@ int check_operands(const void *A, int64_t lda, int transA, const void *B, int64_
     int rc = check_sizes(m, k, p);
     if (rc) return rc;
     if (!valid_dtype(dtype)) return fail(CMM_ERR_ARG, "bad dtype %d", dtype);
-    if (prec != CMM_PREC_F64 && prec != CMM_PREC_F32 && !prec_tc(prec))
+    if (prec != CMM_PREC_F64 && prec != CMM_PREC_F32 && !prec_tc(prec) && prec != CMM_PREC_FX64)
         return fail(CMM_ERR_ARG, "bad precision %d", prec);
     if (transA != 0 && transA != 1) return fail(CMM_ERR_ARG, "transA must be 0 or 1");
     if (m > 0 && k > 0 && !A) return fail(CMM_ERR_ARG, "A is NULL");
@@ -313,7 +323,7 @@ int run_sketch(const void *A, int64_t lda, int transA, const void *B, int64_t ld
         // scatter): A^T rows, then B rows; taken by the preparation kernels
         // where they run, else by a pass over the caller's FP32 rows
         float *cm = colmax + 2 * k0;
-        const bool fx = prec != CMM_PREC_F64 && kp > 0;
+        const bool fx = prec != CMM_PREC_F64 && prec != CMM_PREC_FX64 && kp > 0;
         if (fx && (pl.prep_A || pl.prep_B)) {
             e = cudaMemsetAsync(cm, 0, 2 * kp * sizeof(float), s);
             if (e != cudaSuccess) return cuda_fail(e, "column maxima reset");
@@ -347,7 +357,22 @@ int run_sketch(const void *A, int64_t lda, int transA, const void *B, int64_t ld
         pp.nchunks = pl.pnch[c];
         double *pc = partial + blk0 * hs->d * b;
         blk0 += pl.pnch[c];
-        if (pl.tmem) {
+        if (prec == CMM_PREC_FX64) {
+            // quantise this part's rows of A^T and B to int64 fixed point, then sketch
+            long long *Aq = reinterpret_cast<long long *>(base + pl.off_Aq) + k0 * m;
+            long long *Bq = reinterpret_cast<long long *>(base + pl.off_Bq) + k0 * p;
+            int *expA = reinterpret_cast<int *>(base + pl.off_exp) + k0;
+            int *expB = reinterpret_cast<int *>(base + pl.off_exp) + k + k0;
+            {
+                Span sp("fx_quantize", s, 2);
+                e = launch_fx_quantize((const double *)Atc, pl.ldat, kp, m, Aq, expA, s);
+                if (e == cudaSuccess)
+                    e = launch_fx_quantize((const double *)Bpc, pl.ldbp, kp, p, Bq, expB, s);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "fixed-point quantisation");
+            Span sp("sketch_fx64", s, 2);
+            e = launch_sketch_fx64(pp, Aq, Bq, m, kp, p, hs->d, hp, tabA, tabB, expA, expB, pc, s);
+        } else if (pl.tmem) {
             Span sp("sketch_f32", s);
             e = launch_sketch_tm(pp, (const float *)Atc, (const float *)Bpc, m, kp, p, hs->d, tabA,
                                  tabB, cm, pc, s);

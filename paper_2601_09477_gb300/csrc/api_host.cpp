@@ -39,13 +39,17 @@ int host_parts(int64_t m, int64_t k, int64_t p, size_t es) {
 // c, ratio = sketch time / copy time per inner index.  Per inner index the
 // copy moves (m + p) elements over the host link (~211 GB/s measured on this
 // GPU's host path) and the sketch does d (2 b log2 b + b) butterfly
-// operations (~18 Tops/s FP32, ~13 Tops/s BF16 blocks, ~0.45 Tops/s FP64).
+// operations (~18 Tops/s FP32, ~13 Tops/s BF16 blocks, ~6 Tops/s exact fixed
+// point, ~0.45 Tops/s FP64).
 // Kept within [1/2, 3]: only the first part's copy is exposed, and it shrinks
 // as the later parts grow.
 double host_part_ratio(int64_t m, int64_t p, int d, int L, size_t es, int prec) {
     const double b = std::ldexp(1.0, L);
     const double copy_t = (double)(m + p) * (double)es / 211e9;
-    const double rate = prec == CMM_PREC_F64 ? 0.45e12 : prec_tc(prec) ? 13e12 : 18e12;
+    const double rate = prec == CMM_PREC_F64    ? 0.45e12
+                        : prec == CMM_PREC_FX64 ? 6e12
+                        : prec_tc(prec)         ? 13e12
+                                                : 18e12;
     const double sketch_t = (double)d * (2.0 * b * L + b) / rate;
     return std::min(3.0, std::max(0.5, sketch_t / copy_t));
 }

@@ -40,6 +40,7 @@ using tab_t = uint16_t;
 // Largest transform slice one CTA holds, per butterfly precision.
 constexpr int kMaxLloF32 = 14;   // 2^14 FP32 = 64 KiB of shared memory
 constexpr int kMaxLloF64 = 13;   // 2^13 FP64 = 64 KiB
+constexpr int kMaxLloFx64 = 13;  // 2^13 int64 = 64 KiB (exact fixed-point form)
 constexpr int kFinishLlo = 12;   // FP64 slice of the inverse transform: 2^12 doubles = 32 KiB
 
 // Most parts a sketch is split into along the inner index (the host-buffer
@@ -58,6 +59,8 @@ struct SketchPlan {
     size_t smem;           // dynamic shared memory per CTA
     // workspace carve-up (byte offsets into ws)
     size_t off_At, off_Bp, off_partial, off_Z, off_tab, off_colmax, total;
+    // exact fixed-point form: int64 operands (k x m, k x p) and their row exponents (2k)
+    size_t off_Aq, off_Bq, off_exp;
     bool prep_A, prep_B;   // whether A / B are converted into the workspace
     int64_t ldat, ldbp;    // leading dimensions of the operands the sketch reads
     bool tmem;             // use the TMEM variant of the FP32 kernel
@@ -157,6 +160,18 @@ cudaError_t launch_sketch_fft(const SketchPlan &pl, const float *At, const float
                               cudaStream_t s);
 cudaError_t launch_finish_fft(const double *partial, int nchunks, int d, int L, int C, int NC,
                               double *G, double *R, cudaStream_t s);
+// exact 64-bit fixed-point form (CMM_PREC_FX64, sketch_fx64.cu): rows of X
+// (k x n FP64, leading dimension ldx) quantised to Q (k x n int64) with one
+// power of two 2^expo[t] per row (sum |Q[t][:]| < 2^62); the sketch kernel
+// reads Q and the exponents and builds its own scatter tables (tabA, tabB)
+int sketch_fx64_threads();
+size_t sketch_fx64_smem(int Llo);
+cudaError_t launch_fx_quantize(const double *X, int64_t ldx, int64_t k, int64_t n, long long *Q,
+                               int *expo, cudaStream_t s);
+cudaError_t launch_sketch_fx64(const SketchPlan &pl, const long long *Aq, const long long *Bq,
+                               int64_t m, int64_t k, int64_t p, int d, const HashParams &hp,
+                               tab_t *tabA, tab_t *tabB, const int *expA, const int *expB,
+                               double *partial, cudaStream_t s);
 int sketch_threads_f32(int Llo);
 int sketch_threads_f64(int Llo);
 size_t sketch_smem_f32(int Llo);

@@ -201,7 +201,7 @@ cudaError_t prep_B_t(const void *B, int64_t ldb, int dtype, int64_t k, int64_t p
 
 cudaError_t launch_prep_A(const void *A, int64_t lda, int transA, int dtype, int prec, int64_t m,
                           int64_t k, void *At, int64_t ldat, cudaStream_t s, float *rmax) {
-    if (prec == CMM_PREC_F64)
+    if (prec == CMM_PREC_F64 || prec == CMM_PREC_FX64)   // FP64 copies
         return prep_A_t<double, false>(A, lda, transA, dtype, m, k, (double *)At, ldat, nullptr, s);
     if (rmax) return prep_A_t<float, true>(A, lda, transA, dtype, m, k, (float *)At, ldat, rmax, s);
     return prep_A_t<float, false>(A, lda, transA, dtype, m, k, (float *)At, ldat, nullptr, s);
@@ -238,7 +238,7 @@ cudaError_t launch_rowmax(const float *X, int64_t ldx, int64_t rows, int64_t col
 
 cudaError_t launch_prep_B(const void *B, int64_t ldb, int dtype, int prec, int64_t k, int64_t p,
                           void *Bp, int64_t ldbp, cudaStream_t s, float *rmax) {
-    if (prec == CMM_PREC_F64)
+    if (prec == CMM_PREC_F64 || prec == CMM_PREC_FX64)   // FP64 copies
         return prep_B_t<double, false>(B, ldb, dtype, k, p, (double *)Bp, ldbp, nullptr, s);
     if (rmax) return prep_B_t<float, true>(B, ldb, dtype, k, p, (float *)Bp, ldbp, rmax, s);
     return prep_B_t<float, false>(B, ldb, dtype, k, p, (float *)Bp, ldbp, nullptr, s);

@@ -1,0 +1,440 @@
+// sketch_fx64.cu -- the sketch (Algorithm 1's loop over the inner index t)
+// with exact 64-bit fixed-point butterflies: results within the FP64
+// tolerance of the plain FP64 form, without running the butterflies on the
+// FP64 pipe (which this GPU issues at 1/64 of the FP32 rate).
+//
+// Fixed point.  Column t of A (row t of A^T) is quantised once, before the
+// sketch, as q_i = round(a_i 2^e) with one power of two per column chosen
+// from its l1 norm so that sum_i |q_i| <= 2^61 + m/2 < 2^62.  Every bucket sum
+// of the scatter and every value of the Walsh-Hadamard transform of a slice is
+// then an exact integer of magnitude below 2^62 (|H f|_inf <= |f|_1 <= sum_i
+// |q_i|), so the scatter and all butterflies are exact int64 arithmetic and
+// independent of the order of the atomics.  The only rounding before the
+// multiply is the quantisation, |a_i - q_i 2^-e| <= 2^-(e+1) <= 2^-61 |a|_1,
+// which moves R_r[w] by at most 2^-61 c_max (|A_t|_1 |B_t|_1 + ...) per t --
+// about 2^-45 of sum_t |A_t|_2 |B_t|_2 at m = p = 8192 in the worst case.
+//
+// Multiply-accumulate.  Each transformed value X^ (int64) is split into three
+// 21-bit chunks that convert to FP32 exactly (a magic-number add, no
+// conversion instruction: this GPU converts 64-bit integers at the FP64 rate)
+// and summed error-free into a float-float pair (xh, xl) with xh + xl = X^ to
+// 2^-48.  Products X^ Y^ are formed error-free (FMA) and accumulated over the
+// block of t in float-float (TwoSum), ~2^-46 relative; the block's sum is
+// written as an FP64 partial and the cross-block reduction, the inverse
+// transform and the extraction are FP64 as in every form.
+//
+// Work decomposition as in the other sketch kernels: one CTA = (repetition r,
+// frequency slice u_hi of 2^13 points, block of t); 256 threads, 32 int64
+// values per thread in three register rounds (5 + 5 + 3 index bits); the
+// slice is int64 in shared memory (66 KiB padded), X^ and the running sum Z
+// as float-float in tensor memory (4 words per point, 256 columns), two CTAs
+// per SM.  Scatter: each int64 is added to shared memory as two 32-bit
+// atomics, the low word's carry-out (from the returned old value) added into
+// the high word, which sums the 64-bit values exactly in any order (a 64-bit
+// shared atomic add runs ~6x slower here).
+#include "cmm_internal.h"
+#include "fwht_device.cuh"
+#include "sketch_impl.cuh"
+#include "tmem_device.cuh"
+
+namespace cmm {
+
+namespace {
+
+// ---------------------------------------------------------------- quantisation
+// One CTA per row t of X (k rows of n FP64 values, leading dimension ldx):
+// l1 = sum |X[t][:]| (fixed reduction order: deterministic), e[t] = 61 -
+// (exponent of l1, so that l1 < 2^E), clamped so that 2^e is a normal double,
+// and Q[t][i] = round(X[t][i] 2^e) (int64, leading dimension n).
+constexpr int kQThreads = 256;
+
+__global__ void __launch_bounds__(kQThreads)
+fx_quantize_kernel(const double *__restrict__ X, int64_t ldx, int64_t k, int64_t n,
+                   long long *__restrict__ Q, int *__restrict__ expo) {
+    __shared__ double red[kQThreads / 32];
+    const int tid = threadIdx.x;
+    for (int64_t t = blockIdx.x; t < k; t += gridDim.x) {
+        const double *row = X + t * ldx;
+        double s = 0.0;
+        for (int64_t i = tid; i < n; i += kQThreads) s += fabs(row[i]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((tid & 31) == 0) red[tid >> 5] = s;
+        __syncthreads();
+        double l1 = 0.0;
+#pragma unroll
+        for (int w = 0; w < kQThreads / 32; ++w) l1 += red[w];
+        __syncthreads();
+        int e = 0;
+        if (l1 > 0.0) {
+            int E;
+            frexp(l1, &E);   // l1 < 2^E
+            e = 61 - E;
+            e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
+        }
+        const double sc = __longlong_as_double((long long)(1023 + e) << 52);   // 2^e
+        long long *qrow = Q + t * n;
+        for (int64_t i = tid; i < n; i += kQThreads) qrow[i] = __double2ll_rn(row[i] * sc);
+        if (tid == 0) expo[t] = e;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_fx_quantize(const double *X, int64_t ldx, int64_t k, int64_t n, long long *Q,
+                               int *expo, cudaStream_t s) {
+    if (k <= 0) return cudaSuccess;
+    const int64_t g = k < 152 * 8 ? k : 152 * 8;
+    fx_quantize_kernel<<<(unsigned)g, kQThreads, 0, s>>>(X, ldx, k, n, Q, expo);
+    return cudaGetLastError();
+}
+
+}  // namespace cmm
+
+namespace cmm {
+
+namespace {
+
+// ---------------------------------------------------------------- device helpers
+// 2^ex as a float; 0 below the normal range (such terms are negligible: see
+// the block scale in sketch_fx64_kernel)
+__device__ __forceinline__ float pow2f(int ex) {
+    return ex < -126 ? 0.f : __int_as_float((127 + (ex > 127 ? 127 : ex)) << 23);
+}
+
+// c * s exactly, for |c| < 2^22 and s a power of two (or 0): 1.5 2^23 + c is
+// exact in FP32 (its unit in the last place is 1), so (that - 1.5 2^23) * s
+// is formed by one FMA without rounding
+__device__ __forceinline__ float chunk_f(int c, float s) {
+    const float mf = __int_as_float(0x4B400000 + c);
+    return __fmaf_rn(mf, s, -12582912.f * s);
+}
+
+// v (int64, |v| < 2^63) times 2^ex as a float-float pair h + l: three 21-bit
+// chunks, each exact in FP32; the top two are summed error-free (Fast2Sum:
+// the top chunk's term is 0 or larger than the middle one's) and the bottom
+// chunk is added to the error term
+__device__ __forceinline__ void to_ff(long long v, int ex, float &h, float &l) {
+    const int c2 = (int)(v >> 42);                                  // signed, |c2| <= 2^21
+    const int c1 = (int)((unsigned long long)v >> 21) & 0x1FFFFF;   // 0 .. 2^21 - 1
+    const int c0 = (int)v & 0x1FFFFF;
+    const float a = chunk_f(c2, pow2f(ex + 42));
+    const float b = chunk_f(c1, pow2f(ex + 21));
+    const float c = chunk_f(c0, pow2f(ex));
+    const float s = a + b;
+    const float e = b - (s - a);
+    h = s;
+    l = e + c;
+}
+
+// (zh, zl) += (xh + xl)(yh + yl): the product error-free to ~2^-46, the sum
+// by TwoSum with the errors gathered in zl
+__device__ __forceinline__ void ff_mac(float xh, float xl, float yh, float yl, float &zh,
+                                       float &zl) {
+    const float ph = xh * yh;
+    const float pe = __fmaf_rn(xh, yh, -ph);
+    const float pl = __fmaf_rn(xh, yl, __fmaf_rn(xl, yh, pe));
+    const float s = zh + ph;
+    const float bb = s - zh;
+    const float err = (zh - (s - bb)) + (ph - bb);
+    zl = zl + (err + pl);
+    zh = s;
+}
+
+// 64-bit add of v into the int64 word `idx` of the slice (viewed as 32-bit
+// words) by two 32-bit atomics: the low word's carry-out, read from the old
+// value it returns, goes into the high word with v's high half; the final
+// 64-bit value is the exact sum in any order
+__device__ __forceinline__ void add64_shared(unsigned *S32, uint32_t idx, long long v) {
+    const unsigned lo = (unsigned)v;
+    const unsigned old = atomicAdd(S32 + 2 * idx, lo);
+    const int hi = (int)(v >> 32) + ((old + lo) < old ? 1 : 0);
+    if (hi != 0) atomicAdd(reinterpret_cast<int *>(S32) + 2 * idx + 1, hi);
+}
+
+// scatter one fixed-point column (n int64 values) with the packed table
+// (padded int64 word of the bucket in bits 0-14, sign in bit 15); batches of
+// B values per thread with all loads first
+template <int P, int B = 8>
+__device__ __forceinline__ void scatter_fx(unsigned *S32, const long long *__restrict__ col,
+                                           const tab_t *__restrict__ tab, int64_t n, int q) {
+    int64_t i = q;
+    for (; i + (B - 1) * (int64_t)P < n; i += B * (int64_t)P) {
+        long long v[B];
+        tab_t w[B];
+#pragma unroll
+        for (int e = 0; e < B; ++e) {
+            v[e] = __ldcs(col + i + e * (int64_t)P);
+            w[e] = __ldg(tab + i + e * (int64_t)P);
+        }
+#pragma unroll
+        for (int e = 0; e < B; ++e) add64_shared(S32, w[e] & 0x7fffu, (w[e] >> 15) ? -v[e] : v[e]);
+    }
+    if (i < n) {
+        long long v[B];
+        tab_t w[B];
+#pragma unroll
+        for (int e = 0; e < B; ++e) {
+            const bool ok = i + e * (int64_t)P < n;
+            v[e] = ok ? __ldcs(col + i + e * (int64_t)P) : 0ll;
+            w[e] = ok ? __ldg(tab + i + e * (int64_t)P) : (tab_t)0;
+        }
+#pragma unroll
+        for (int e = 0; e < B; ++e)
+            if (i + e * (int64_t)P < n)
+                add64_shared(S32, w[e] & 0x7fffu, (w[e] >> 15) ? -v[e] : v[e]);
+    }
+}
+
+
+// ---------------------------------------------------------------- the sketch kernel
+constexpr int kFxThreads = 256;
+
+template <int L>
+struct FxCfg {
+    static constexpr int LE = L < 5 ? L : 5;
+    using S = FwhtShape<long long, L, LE>;
+    static constexpr int E = S::E, P = S::P, G = kFxThreads / P;
+    static constexpr bool TM = LE == 5;   // X^ and Z in tensor memory (else registers)
+    static constexpr uint32_t COLS = 256; // 4 words per point, 2 threads per TMEM lane
+    static constexpr size_t SMEM = (size_t)G * S::STRIDE * sizeof(long long);
+    static_assert(kFxThreads % P == 0, "CTA must hold whole groups");
+    static_assert((size_t)S::N * sizeof(double) <= SMEM, "FP64 reduction must fit");
+};
+
+// One CTA: repetition r, slice u_hi, inner indices [t0, t1) of the block.
+// Aq / Bq: fixed-point operands (k x m, k x p int64), expA / expB their
+// per-row exponents; tables as for the FP32 kernels (int64 word layout).
+template <int L>
+__global__ void __launch_bounds__(kFxThreads, 2)
+sketch_fx64_kernel(const long long *__restrict__ Aq, const long long *__restrict__ Bq,
+                   int64_t m, int64_t k, int64_t p, int Lfull, int C, int64_t chunk, int d,
+                   const tab_t *__restrict__ tabA, const tab_t *__restrict__ tabB,
+                   const int *__restrict__ expA, const int *__restrict__ expB,
+                   double *__restrict__ partial) {
+    using Cfg = FxCfg<L>;
+    using S = typename Cfg::S;
+    constexpr int E = Cfg::E, P = Cfg::P, G = Cfg::G, LE = Cfg::LE;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint32_t s_taddr;
+    __shared__ int s_red[kFxThreads / 32];
+
+    int item = blockIdx.x;
+    const uint32_t u_hi = (uint32_t)(item % C);
+    item /= C;
+    const int r = item % d;
+    const int64_t blk = item / d;
+    const int64_t t0 = blk * chunk;
+    const int64_t t1 = (t0 + chunk < k) ? t0 + chunk : k;
+    const int64_t b = (int64_t)1 << Lfull;
+    const int64_t slot = (int64_t)r * C + u_hi;
+    const tab_t *tA = tabA + slot * m;
+    const tab_t *tB = tabB + slot * p;
+    double *out = partial + (blk * d + r) * b + (int64_t)u_hi * S::N;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int g = tid / P, q = tid % P;
+    long long *sm = reinterpret_cast<long long *>(smem_raw);
+    long long *Sg = sm + g * S::STRIDE;
+    unsigned *S32 = reinterpret_cast<unsigned *>(Sg);
+
+    if constexpr (Cfg::TM) {
+        if (warp == 0) tm::alloc(&s_taddr, Cfg::COLS);
+    }
+    for (int i = tid; i < G * S::STRIDE; i += kFxThreads) sm[i] = 0;
+    // block scale: S_ref = max over the block's t of 64 - eA_t - eB_t
+    int mx = -0x40000000;
+    for (int64_t t = t0 + tid; t < t1; t += kFxThreads) mx = max(mx, 64 - expA[t] - expB[t]);
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((tid & 31) == 0) s_red[warp] = mx;
+    if constexpr (Cfg::TM) tm::fence_before();
+    __syncthreads();
+    if constexpr (Cfg::TM) tm::fence_after();
+    int sref = s_red[0];
+#pragma unroll
+    for (int w = 1; w < kFxThreads / 32; ++w) sref = max(sref, s_red[w]);
+    if (t1 <= t0) sref = 0;
+
+    // this thread's TMEM columns: lane 32 (warp mod 4) + lane id, column block
+    // 128 (warp / 4): xh [0, E), xl [E, 2E), zh [2E, 3E), zl [3E, 4E)
+    uint32_t tcol = 0;
+    float xr[2 * E], zr[2 * E];   // register copies when the slice is small
+    if constexpr (Cfg::TM) {
+        tcol = s_taddr + ((uint32_t)(32 * (warp & 3)) << 16) + 128u * (uint32_t)(warp >> 2);
+        uint32_t zero[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) zero[e] = 0u;
+#pragma unroll
+        for (int c = 0; c < 2 * E / 16; ++c) tm::st16(tcol + 2 * E + 16 * c, zero);
+        tm::wait_st();
+    } else {
+#pragma unroll
+        for (int j = 0; j < 2 * E; ++j) zr[j] = 0.f;
+    }
+
+    long long v[E];
+    const int64_t nt = t1 > t0 ? t1 - t0 : 0;
+    const int64_t iters = (nt + G - 1) / G;   // the same trip count for every group
+    for (int64_t it = 0; it < iters; ++it) {
+        const int64_t t = t0 + it * G + g;
+        const bool active = t < t1;
+        // A's values carry the block scale 2^(64 - eA - eB - S_ref) <= 1 and
+        // 2^-32 (keeps the float-float products and sums in range)
+        const int exA = active ? (64 - expA[t] - expB[t] - sref) - 32 : -1000;
+        if (active) scatter_fx<P>(S32, Aq + t * m, tA, m, q);
+        group_sync<P>(g);
+        fwht_rounds<long long, L, LE, 0>(Sg, v, q, g);
+        if constexpr (Cfg::TM) {
+#pragma unroll
+            for (int c = 0; c < E / 16; ++c) {
+                uint32_t hw[16], lw[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    float h, l;
+                    to_ff(v[16 * c + e], exA, h, l);
+                    hw[e] = __float_as_uint(h);
+                    lw[e] = __float_as_uint(l);
+                }
+                tm::st16(tcol + 16 * c, hw);
+                tm::st16(tcol + E + 16 * c, lw);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < E; ++j) to_ff(v[j], exA, xr[j], xr[E + j]);
+        }
+        group_sync<P>(g);
+        if (active) scatter_fx<P>(S32, Bq + t * p, tB, p, q);
+        group_sync<P>(g);
+        fwht_rounds<long long, L, LE, 0>(Sg, v, q, g);
+        if constexpr (Cfg::TM) {
+            tm::wait_st();
+#pragma unroll
+            for (int c = 0; c < E / 16; ++c) {
+                uint32_t hw[16], lw[16], zh[16], zl[16];
+                tm::ld16(tcol + 16 * c, hw);
+                tm::ld16(tcol + E + 16 * c, lw);
+                tm::ld16(tcol + 2 * E + 16 * c, zh);
+                tm::ld16(tcol + 3 * E + 16 * c, zl);
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    float yh, yl;
+                    to_ff(v[16 * c + e], -32, yh, yl);
+                    float a = __uint_as_float(zh[e]), bz = __uint_as_float(zl[e]);
+                    ff_mac(__uint_as_float(hw[e]), __uint_as_float(lw[e]), yh, yl, a, bz);
+                    zh[e] = __float_as_uint(a);
+                    zl[e] = __float_as_uint(bz);
+                }
+                tm::st16(tcol + 2 * E + 16 * c, zh);
+                tm::st16(tcol + 3 * E + 16 * c, zl);
+            }
+            tm::wait_st();
+        } else {
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                float yh, yl;
+                to_ff(v[j], -32, yh, yl);
+                ff_mac(xr[j], xr[E + j], yh, yl, zr[j], zr[E + j]);
+            }
+        }
+        group_sync<P>(g);
+    }
+
+    // the block's Z = (zh + zl) 2^S_ref in FP64
+    double zd[E];
+    if constexpr (Cfg::TM) {
+#pragma unroll
+        for (int c = 0; c < E / 16; ++c) {
+            uint32_t zh[16], zl[16];
+            tm::ld16(tcol + 2 * E + 16 * c, zh);
+            tm::ld16(tcol + 3 * E + 16 * c, zl);
+#pragma unroll
+            for (int e = 0; e < 16; ++e)
+                zd[16 * c + e] = scalbn((double)__uint_as_float(zh[e]) +
+                                        (double)__uint_as_float(zl[e]), sref);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < E; ++j) zd[j] = scalbn((double)zr[j] + (double)zr[E + j], sref);
+    }
+    if constexpr (G == 1) {
+#pragma unroll
+        for (int j = 0; j < E; ++j) out[final_index<long long, L, LE>(q, j)] = zd[j];
+    } else {
+        __syncthreads();
+        double *acc = reinterpret_cast<double *>(smem_raw);
+        for (int i = tid; i < S::N; i += kFxThreads) acc[i] = 0.0;
+        __syncthreads();
+        for (int gg = 0; gg < G; ++gg) {
+            if (g == gg) {
+#pragma unroll
+                for (int j = 0; j < E; ++j) acc[final_index<long long, L, LE>(q, j)] += zd[j];
+            }
+            __syncthreads();
+        }
+        for (int i = tid; i < S::N; i += kFxThreads) out[i] = acc[i];
+    }
+    if constexpr (Cfg::TM) {
+        tm::fence_before();
+        __syncthreads();
+        tm::fence_after();
+        if (warp == 0) tm::dealloc(s_taddr, Cfg::COLS);
+    }
+}
+
+template <int L>
+cudaError_t run_fx(const SketchPlan &pl, const long long *Aq, const long long *Bq, int64_t m,
+                   int64_t k, int64_t p, int d, const HashParams &hp, tab_t *tabA, tab_t *tabB,
+                   const int *expA, const int *expB, double *partial, cudaStream_t s) {
+    using Cfg = FxCfg<L>;
+    {
+        const int64_t n = (int64_t)d * pl.C * (m + p);
+        int64_t gt = (n + 255) / 256;
+        if (gt > 152 * 32) gt = 152 * 32;
+        if (gt < 1) gt = 1;
+        sketch_table_kernel<long long, L, Cfg::LE><<<(unsigned)gt, 256, 0, s>>>(
+            hp, d, pl.L, L, pl.C, m, p, tabA, tabB);
+        cudaError_t e0 = cudaGetLastError();
+        if (e0 != cudaSuccess) return e0;
+    }
+    auto kern = sketch_fx64_kernel<L>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Cfg::SMEM);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (int64_t)pl.nchunks * d * pl.C;
+    kern<<<(unsigned)blocks, kFxThreads, Cfg::SMEM, s>>>(Aq, Bq, m, k, p, pl.L, pl.C, pl.chunk, d,
+                                                       tabA, tabB, expA, expB, partial);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+}  // namespace cmm
+
+namespace cmm {
+
+int sketch_fx64_threads() { return kFxThreads; }
+
+size_t sketch_fx64_smem(int Llo) {
+    switch (Llo) {
+#define CASE(L) case L: return FxCfg<L>::SMEM;
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10)
+        CASE(11) CASE(12) CASE(13)
+#undef CASE
+    }
+    return 0;
+}
+
+cudaError_t launch_sketch_fx64(const SketchPlan &pl, const long long *Aq, const long long *Bq,
+                               int64_t m, int64_t k, int64_t p, int d, const HashParams &hp,
+                               tab_t *tabA, tab_t *tabB, const int *expA, const int *expB,
+                               double *partial, cudaStream_t s) {
+    switch (pl.Llo) {
+#define CASE(L) case L: return run_fx<L>(pl, Aq, Bq, m, k, p, d, hp, tabA, tabB, expA, expB, partial, s);
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10)
+        CASE(11) CASE(12) CASE(13)
+#undef CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace cmm

@@ -25,7 +25,7 @@ static void check_round(int threads) {
     using RK = typename S::template Round<K>;
     constexpr int N = S::N, E = S::E, P = S::P;
     const int G = threads / P;
-    const char *tn = sizeof(T) == 4 ? "f32" : "f64";
+    const char *tn = sizeof(T) == 4 ? "f32" : "64-bit";
     if (G < 1 || threads % P != 0) {
         std::printf("%s L=%d LE=%d threads=%d: groups do not tile the CTA\n", tn, L, LE, threads);
         ++g_fail;
@@ -129,6 +129,8 @@ static void all_l() {
     // single-problem sketch kernels
     check<float, L, LE32>(L == 14 ? 512 : 256);
     if constexpr (L <= 13) check<double, L, LE64>(L == 13 ? 512 : 256);
+    // exact fixed-point (int64) sketch kernel: 256 threads, 32 values per thread
+    if constexpr (L <= 13) check<long long, L, LE32>(256);
     // batched sketch tasks: 512 threads, slices 2^5 .. 2^14
     if constexpr (L >= 5) check<float, L, 5>(512);
     // adjoint kernel: max(P, 256) threads
