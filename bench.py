@@ -35,7 +35,11 @@ if ROOT not in sys.path:
 
 METRIC = "sketch+FWHT+extract ms & % HBM roofline; speedup vs plain FP64 at equal error"
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC_PATH = os.path.join(ROOT, "profiles", "sketch_f32_n8192_traffic.json")
+def traffic_path(prec: str, n: int) -> str:
+    """ncu DRAM traffic of one sketch launch, stored by the profiling summary."""
+    return os.path.join(ROOT, "profiles", "sketch_%s_n%d_traffic.json" % (prec, n))
+
+
 FALLBACK_HBM_GBS = 6800.0
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
@@ -50,7 +54,10 @@ def parse():
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--log2b", type=int, default=16)
     ap.add_argument("--d", type=int, default=9)
-    ap.add_argument("--prec", default="f32", choices=["f32", "f64", "bf16tc", "f16tc"])
+    ap.add_argument("--prec", default="fx64", choices=["f32", "f64", "fx64", "bf16tc", "f16tc"],
+                    help="arithmetic of the timed step (default: the exact fixed-point form, within the FP64 tolerance)")
+    ap.add_argument("--compare-steps", type=int, default=3,
+                    help="timed steps of each other form (FP32, plain FP64) on the same input")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-dgemm", action="store_true", help="skip the cuBLAS DGEMM comparison")
     ap.add_argument("--no-e2e", action="store_true")
@@ -81,6 +88,7 @@ def workload_config(a):
                     "b=2^%d, d=%d, median, heavy hitters |C|>=n/2" % (a.n, a.log2b, a.d),
         "n": a.n, "m": a.n, "k": a.n, "p": a.n, "log2b": a.log2b, "d": a.d,
         "tau": a.n / 2, "input_dtype": "f64", "l2": l2,
+        "arithmetic": FORM_OF.get(getattr(a, "prec", "fx64"), ""),
         "parallelism": "replicas (one problem per GPU)",
     }
 
@@ -94,9 +102,14 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback", {}
 
 
-def source_hash():
+def source_hash(prec: str = "f32"):
+    """Hash of the sources of a form's sketch kernel (a stored traffic figure is
+    used only while they are unchanged)."""
     h = hashlib.sha256()
-    for name in ["sketch_impl.cuh", "fwht_device.cuh", "sketch_f32.cu", "sketch_tm.cu"]:
+    names = (["sketch_fx64.cu", "fwht_device.cuh", "tmem_device.cuh", "sketch_impl.cuh"]
+             if prec == "fx64" else
+             ["sketch_impl.cuh", "fwht_device.cuh", "sketch_f32.cu", "sketch_tm.cu"])
+    for name in names:
         with open(os.path.join(ROOT, "paper_2601_09477_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -118,6 +131,41 @@ def alu_roofline(kernel: str, ops: float, ms: float, note: str = "") -> dict:
     if note:
         out["ops_counted"] = note
     return out
+
+
+# the arithmetic each form computes in, and its name
+DTYPE_OF = {"fx64": "int64", "f32": "f32", "f64": "f64", "bf16tc": "bf16", "f16tc": "f16"}
+FORM_OF = {"fx64": "exact 64-bit fixed-point butterflies, float-float multiply-accumulate, FP64 "
+                   "reduction/inverse/extraction (FP64 tolerance)",
+           "f32": "FP32 butterflies (fixed-point scatter), FP64 reduction/inverse/extraction",
+           "f64": "plain FP64 butterflies and accumulation",
+           "bf16tc": "BF16 tensor-core Hadamard blocks, FP32 accumulation",
+           "f16tc": "FP16 tensor-core Hadamard blocks, FP32 accumulation"}
+
+
+def alu_roofline_for(prec: str, kernel: str, ops: float, ms: float) -> dict:
+    """Roofline object of a sketch kernel: its algorithmic operations per launch
+    (butterfly add/subs of both sketches and one multiply-accumulate per
+    bucket) over its average launch time, against the peak of the unit the
+    form's butterflies run on: FP32 lanes (FP32 and tensor-core forms), 32-bit
+    integer lanes at two instructions per 64-bit add (exact fixed point), or
+    the FP64 pipe (plain FP64)."""
+    _, _, pk = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    lanes = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6
+    if prec == "fx64":
+        peak, src = lanes / 2 / 1e12, ("152 SMs x 128 integer lanes x %g MHz / 2 instructions "
+                                       "per 64-bit add" % sm_max)
+    elif prec == "f64":
+        peak, src = SM_COUNT * 2 * sm_max * 1e6 / 1e12, ("152 SMs x 2 FP64 adds per clock x %g "
+                                                         "MHz" % sm_max)
+    else:
+        peak, src = lanes / 1e12, "152 SMs x 128 FP32 lanes x %g MHz max SM clock" % sm_max
+    achieved = ops / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+    return {"bound": "alu", "kernel": kernel, "achieved": round(achieved, 3),
+            "peak": round(peak, 3), "unit": "Tops/s", "frac": round(achieved / peak, 4),
+            "traffic": None, "ops_per_launch": ops, "peak_source": src,
+            "avg_launch_ms": round(ms, 4)}
 
 
 def cpu_model() -> str:
@@ -247,7 +295,7 @@ def oracle_sample(A, B, hp, log2b, n, d, tau, k_sample, rows_sample, threads):
     return ms, sample, (t2 - t0)
 
 
-def oracle_step(A, B, hp, log2b, n, d, tau, threads):
+def oracle_step(A, B, hp, log2b, n, d, tau, threads, with_R=False):
     """One whole step of the FP64 oracle on the host cores: Compress over all
     inner indices, Decompress of every entry, and the heavy-hitter list
     {(i, j) : |Chat_ij| >= tau} of that estimate.  Returns its time in ms."""
@@ -257,7 +305,10 @@ def oracle_step(A, B, hp, log2b, n, d, tau, threads):
     C = orc.extract(R, hp, n, n, nthreads=threads)
     I, J = np.nonzero(np.abs(C) >= tau)
     del C, I, J
-    return (time.perf_counter() - t0) * 1e3
+    ms = (time.perf_counter() - t0) * 1e3
+    if with_R:
+        return ms, R
+    return ms
 
 
 # wall-clock bound of the reference arm's timed steps: the arm stops early (and
@@ -380,31 +431,23 @@ def run_cmm(a):
     offdiag = sum(1 for (i, j) in found if i != j)
     recall = sum(1 for q in planted if q in found) / len(planted)
 
-    # dominant kernel and its roofline (ALU-bound FP32 butterflies)
+    # dominant kernel and its roofline (ALU-bound butterflies)
     sk_name = "sketch_" + a.prec
     launches = sum(v[0] for v in trace.values())
     sk_launches, sk_ms_total = trace.get(sk_name, (0, 0.0))
     sk_ms = sk_ms_total / a.steps   # one sketch call per step
     b = 1 << L
-    ops = d * n * (2.0 * b * L + b)   # butterfly add/sub of both sketches + one FMA per bucket
+    ops = d * n * (2.0 * b * L + b)   # butterfly add/sub of both sketches + one MAC per bucket
     hbm_gbs, hbm_kind, pk = peaks()
-    sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12   # Tops/s
-    achieved = ops / (sk_ms * 1e-3) / 1e12
-    traffic = None
+    roofline = alu_roofline_for(a.prec, sk_name, ops, sk_ms)
     try:
-        with open(TRAFFIC_PATH) as f:
+        with open(traffic_path(a.prec, n)) as f:
             tj = json.load(f)
-        if (a.prec == "f32" and tj.get("source_hash") == source_hash() and tj.get("n") == n
-                and tj.get("log2b") == L):
-            traffic = tj.get("dram_bytes_per_launch")
+        if (tj.get("prec", "f32") == a.prec and tj.get("source_hash") == source_hash(a.prec)
+                and tj.get("n") == n and tj.get("log2b") == L):
+            roofline["traffic"] = tj.get("dram_bytes_per_launch")
     except Exception:
         pass
-    roofline = {"bound": "alu", "kernel": sk_name, "achieved": round(achieved, 3),
-                "peak": round(alu_peak, 3), "unit": "Tops/s", "frac": round(achieved / alu_peak, 4),
-                "traffic": traffic, "ops_per_launch": ops,
-                "peak_source": "152 SMs x 128 FP32 lanes x %.0f MHz max SM clock" % sm_max,
-                "avg_launch_ms": round(sk_ms, 4)}
     ab_bytes = 2.0 * n * n * 8
     hbm = {"bytes_A_B": ab_bytes, "achieved_gbs": round(ab_bytes / (ms * 1e-3) / 1e9, 2),
            "peak_gbs": hbm_gbs, "peak_kind": hbm_kind,
@@ -414,7 +457,8 @@ def run_cmm(a):
               "n_gpus": world, "ms_per_problem_whole_job": round(whole_job_ms(ms, world), 4),
               "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms, 4),
               "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-              "dtype": a.prec, "data": "synthetic", "config": workload_config(a),
+              "dtype": DTYPE_OF[a.prec], "precision_form": FORM_OF[a.prec],
+              "data": "synthetic", "config": workload_config(a),
               "roofline": roofline, "hbm_roofline": hbm, "gpu_launches": int(launches),
               "clocks": clk, "kernels_ms_per_step": {k: round(v[1] / a.steps, 4)
                                                      for k, v in sorted(trace.items())},
@@ -424,27 +468,44 @@ def run_cmm(a):
               "step_ms_min": round(per_step[0], 4),
               "step_ms_median": round(per_step[len(per_step) // 2], 4)}
 
-    # plain FP64 form on the same input: time and R agreement
-    if not a.no_fp64 and a.prec != "f64":
-        R32 = R.clone()
-        step("f64")
-        torch.cuda.synchronize()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        step("f64")
-        f1.record(stream)
-        torch.cuda.synchronize()
-        f64_ms = f0.elapsed_time(f1)
-        dR = float((R32 - R).abs().max().item())
-        result["fp64"] = {"ms_per_step": round(f64_ms, 3), "speedup": round(f64_ms / ms, 2),
-                          "max_abs_R_diff_vs_fp32": dR,
-                          "equal_error": dR == 0.0}
+    # the other forms on the same input, each over --compare-steps timed steps
+    # after one warm-up step, with its own clock record: time, the sketch
+    # kernel's roofline, and its R (compared with the oracle's below)
+    R_main = R.clone()
+    forms = {}
+    if not a.no_fp64:
+        for prec in [pr for pr in ("f32", "f64") if pr != a.prec]:
+            step(prec)
+            torch.cuda.synchronize()
+            ck = ClockSampler(local)
+            ck.start()
+            cmm.trace_enable(True)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(a.compare_steps + 1)]
+            ev[0].record(stream)
+            for q in range(a.compare_steps):
+                step(prec)
+                ev[q + 1].record(stream)
+            torch.cuda.synchronize()
+            cmm.trace_enable(False)
+            tr = cmm.trace_read()
+            times = sorted(ev[q].elapsed_time(ev[q + 1]) for q in range(a.compare_steps))
+            f_ms = float(np.mean(times))
+            k_ms = tr.get("sketch_" + prec, (0, 0.0))[1] / a.compare_steps
+            forms[prec] = {"form": FORM_OF[prec], "dtype": DTYPE_OF[prec],
+                           "ms_per_step": round(f_ms, 3), "step_ms_min": round(times[0], 3),
+                           "step_ms_median": round(times[len(times) // 2], 3),
+                           "steps": a.compare_steps, "clocks": ck.stop(),
+                           "roofline": alu_roofline_for(prec, "sketch_" + prec, ops, k_ms),
+                           "speedup_of_headline": round(f_ms / ms, 2),
+                           "R": R.clone()}
+        result["forms"] = forms
+        if "f64" in forms:
+            result["speedup_vs_plain_fp64"] = forms["f64"]["speedup_of_headline"]
 
     # the heavy-hitter list straight from the sketch, without writing C
     # (cmm_heavy_hitters on the step's R): same list as the step's
     if world == 1:
-        hfn = lambda: cmm.heavy_hitters(R, h, n, n, tau, capacity=cap)
+        hfn = lambda: cmm.heavy_hitters(R_main, h, n, n, tau, capacity=cap)
         I2, J2, V2 = hfn()
         same = bool(torch.equal(I2.cpu(), I.cpu()) and torch.equal(J2.cpu(), J.cpu())
                     and torch.equal(V2.cpu(), V.cpu()))
@@ -510,8 +571,16 @@ def run_cmm(a):
         from oracle import oracle as orc
         threads = orc.max_threads()
         # the whole step at the benchmark size takes the oracle about 5 s on 16 cores
-        cpu_ms = oracle_step(A_np, B_np, h.params, L, n, d, tau, threads)
+        cpu_ms, R_orc = oracle_step(A_np, B_np, h.params, L, n, d, tau, threads, with_R=True)
         secs = cpu_ms / 1e3
+        # every form's R against the oracle's, relative to sum_t ||A_t|| ||B_t||
+        scale = float(np.sum(np.linalg.norm(A_np, axis=0) * np.linalg.norm(B_np, axis=1)))
+        result["R_error_vs_oracle"] = {
+            a.prec: float(np.abs(R_main.cpu().numpy() - R_orc).max() / scale)}
+        for prec, fm in forms.items():
+            result["R_error_vs_oracle"][prec] = float(
+                np.abs(fm["R"].cpu().numpy() - R_orc).max() / scale)
+        result["R_error_vs_oracle"]["relative_to"] = "sum_t ||A[:,t]|| ||B[t,:]||"
         sample = ("the whole step, unscaled: Compress over all %d inner indices, Decompress of "
                   "all %d x %d entries and the heavy-hitter list, FP64, %d threads"
                   % (n, n, n, threads))
@@ -526,6 +595,8 @@ def run_cmm(a):
                                   "one_core": {"value": round(one_ms, 1), "unit": "ms",
                                                "sample": one_sample,
                                                "sample_seconds": round(one_secs, 2)}}
+    for fm in forms.values():
+        fm.pop("R", None)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:

@@ -26,7 +26,9 @@
 // Work decomposition as in the other sketch kernels: one CTA = (repetition r,
 // frequency slice u_hi of 2^13 points, block of t); 256 threads, 32 int64
 // values per thread in three register rounds (5 + 5 + 3 index bits); the
-// slice is int64 in shared memory (66 KiB padded), X^ and the running sum Z
+// slice's int64 values are two 32-bit arrays in shared memory (low and high
+// halves, 2 x 36 KiB padded, so that the scatter's atomics spread over all 32
+// banks and round 0 reads 16-byte vectors), X^ and the running sum Z
 // as float-float in tensor memory (4 words per point, 256 columns), two CTAs
 // per SM.  Scatter: each int64 is added to shared memory as two 32-bit
 // atomics, the low word's carry-out (from the returned old value) added into
@@ -44,9 +46,29 @@ namespace {
 // ---------------------------------------------------------------- quantisation
 // One CTA per row t of X (k rows of n FP64 values, leading dimension ldx):
 // l1 = sum |X[t][:]| (fixed reduction order: deterministic), e[t] = 61 -
-// (exponent of l1, so that l1 < 2^E), clamped so that 2^e is a normal double,
-// and Q[t][i] = round(X[t][i] 2^e) (int64, leading dimension n).
+// (exponent of l1, so that l1 < 2^E), clamped to [-1022, 1023], and
+// Q[t][i] = round(X[t][i] 2^e) (int64, leading dimension n).
 constexpr int kQThreads = 256;
+
+// round(a 2^e) for |a 2^e| < 2^62, with integer operations on the bits of a
+// (a conversion instruction from FP64 runs at the FP64 rate here): a =
+// mant 2^(ex - 1075), so a 2^e = mant 2^sh with sh = ex - 1075 + e; halves
+// round away from zero
+__device__ __forceinline__ long long quantize_bits(double a, int e) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(a);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    unsigned long long mant = bits & 0xFFFFFFFFFFFFFull;
+    if (ex) mant |= 1ull << 52;
+    const int sh = (ex ? ex : 1) - 1075 + e;
+    unsigned long long q;
+    if (sh >= 0)
+        q = sh < 11 ? mant << sh : 0ull;   // cannot happen for |a 2^e| < 2^62 beyond 9
+    else if (sh > -64)
+        q = (mant + (1ull << (-sh - 1))) >> (-sh);
+    else
+        q = 0ull;
+    return (bits >> 63) ? -(long long)q : (long long)q;
+}
 
 __global__ void __launch_bounds__(kQThreads)
 fx_quantize_kernel(const double *__restrict__ X, int64_t ldx, int64_t k, int64_t n,
@@ -72,9 +94,8 @@ fx_quantize_kernel(const double *__restrict__ X, int64_t ldx, int64_t k, int64_t
             e = 61 - E;
             e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
         }
-        const double sc = __longlong_as_double((long long)(1023 + e) << 52);   // 2^e
         long long *qrow = Q + t * n;
-        for (int64_t i = tid; i < n; i += kQThreads) qrow[i] = __double2ll_rn(row[i] * sc);
+        for (int64_t i = tid; i < n; i += kQThreads) qrow[i] = quantize_bits(row[i], e);
         if (tid == 0) expo[t] = e;
     }
 }
@@ -141,22 +162,60 @@ __device__ __forceinline__ void ff_mac(float xh, float xl, float yh, float yl, f
     zh = s;
 }
 
-// 64-bit add of v into the int64 word `idx` of the slice (viewed as 32-bit
-// words) by two 32-bit atomics: the low word's carry-out, read from the old
-// value it returns, goes into the high word with v's high half; the final
-// 64-bit value is the exact sum in any order
-__device__ __forceinline__ void add64_shared(unsigned *S32, uint32_t idx, long long v) {
-    const unsigned lo = (unsigned)v;
-    const unsigned old = atomicAdd(S32 + 2 * idx, lo);
-    const int hi = (int)(v >> 32) + ((old + lo) < old ? 1 : 0);
-    if (hi != 0) atomicAdd(reinterpret_cast<int *>(S32) + 2 * idx + 1, hi);
+// to_ff and ff_mac on two values at once with packed FP32x2 instructions
+// (identical results: each lane is an IEEE operation of its own)
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ float2 chunk_f2(int c0, int c1, float s) {
+    const float2 mf = make_float2(__int_as_float(0x4B400000 + c0), __int_as_float(0x4B400000 + c1));
+    const float2 ss = make_float2(s, s);
+    const float2 k = make_float2(-12582912.f * s, -12582912.f * s);
+    return __ffma2_rn(mf, ss, k);
+}
+
+__device__ __forceinline__ void to_ff2(long long v0, long long v1, float s42, float s21,
+                                       float s0, float2 &h, float2 &l) {
+    const float2 a = chunk_f2((int)(v0 >> 42), (int)(v1 >> 42), s42);
+    const float2 b = chunk_f2((int)((unsigned long long)v0 >> 21) & 0x1FFFFF,
+                              (int)((unsigned long long)v1 >> 21) & 0x1FFFFF, s21);
+    const float2 c = chunk_f2((int)v0 & 0x1FFFFF, (int)v1 & 0x1FFFFF, s0);
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 sm = __fadd2_rn(a, b);
+    const float2 e = __ffma2_rn(__ffma2_rn(a, m1, sm), m1, b);   // b - (s - a)
+    h = sm;
+    l = __fadd2_rn(e, c);
+}
+
+__device__ __forceinline__ void ff_mac2(float2 xh, float2 xl, float2 yh, float2 yl, float2 &zh,
+                                        float2 &zl) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 ph = __fmul2_rn(xh, yh);
+    const float2 pe = __ffma2_rn(xh, yh, neg2(ph));
+    const float2 pl = __ffma2_rn(xh, yl, __ffma2_rn(xl, yh, pe));
+    const float2 sm = __fadd2_rn(zh, ph);
+    const float2 bb = __ffma2_rn(zh, m1, sm);                     // s - zh
+    const float2 e1 = __ffma2_rn(__ffma2_rn(bb, m1, sm), m1, zh); // zh - (s - bb)
+    const float2 e2 = __ffma2_rn(bb, m1, ph);                     // ph - bb
+    zl = __fadd2_rn(zl, __fadd2_rn(__fadd2_rn(e1, e2), pl));
+    zh = sm;
+}
+
+// 64-bit add of v into word `idx` of the slice, held as two 32-bit arrays
+// (low and high halves), by two 32-bit atomics: the low word's carry-out,
+// read from the old value it returns, goes into the high word with v's high
+// half; the final 64-bit value is the exact sum in any order
+__device__ __forceinline__ void add64_shared(unsigned *lo, int *hi, uint32_t idx, long long v) {
+    const unsigned l = (unsigned)v;
+    const unsigned old = atomicAdd(lo + idx, l);
+    const int h = (int)(v >> 32) + ((old + l) < old ? 1 : 0);
+    if (h != 0) atomicAdd(hi + idx, h);
 }
 
 // scatter one fixed-point column (n int64 values) with the packed table
-// (padded int64 word of the bucket in bits 0-14, sign in bit 15); batches of
+// (padded word of the bucket in bits 0-14, sign in bit 15); batches of
 // B values per thread with all loads first
 template <int P, int B = 8>
-__device__ __forceinline__ void scatter_fx(unsigned *S32, const long long *__restrict__ col,
+__device__ __forceinline__ void scatter_fx(unsigned *lo, int *hi, const long long *__restrict__ col,
                                            const tab_t *__restrict__ tab, int64_t n, int q) {
     int64_t i = q;
     for (; i + (B - 1) * (int64_t)P < n; i += B * (int64_t)P) {
@@ -168,7 +227,7 @@ __device__ __forceinline__ void scatter_fx(unsigned *S32, const long long *__res
             w[e] = __ldg(tab + i + e * (int64_t)P);
         }
 #pragma unroll
-        for (int e = 0; e < B; ++e) add64_shared(S32, w[e] & 0x7fffu, (w[e] >> 15) ? -v[e] : v[e]);
+        for (int e = 0; e < B; ++e) add64_shared(lo, hi, w[e] & 0x7fffu, (w[e] >> 15) ? -v[e] : v[e]);
     }
     if (i < n) {
         long long v[B];
@@ -182,10 +241,77 @@ __device__ __forceinline__ void scatter_fx(unsigned *S32, const long long *__res
 #pragma unroll
         for (int e = 0; e < B; ++e)
             if (i + e * (int64_t)P < n)
-                add64_shared(S32, w[e] & 0x7fffu, (w[e] >> 15) ? -v[e] : v[e]);
+                add64_shared(lo, hi, w[e] & 0x7fffu, (w[e] >> 15) ? -v[e] : v[e]);
     }
 }
 
+
+// The 2^L-point transform of a group's slice held as two 32-bit arrays (low
+// and high halves of the int64 values, the padded FP32 word layout of
+// fwht_device.cuh), leaving the result in v (last-round layout) and the
+// arrays zeroed for the next scatter.  Round 0 reads its contiguous rows as
+// 16-byte vectors; the last round (of two or more) reads each word and zeroes
+// it by one exchange, so no clearing pass is needed.
+template <int L, int LE, int K>
+__device__ __forceinline__ void fx_rounds(int *lo, int *hi, long long (&v)[1 << LE], int q,
+                                          int g) {
+    using S = FwhtShape<float, L, LE>;
+    using RK = typename S::template Round<K>;
+    constexpr int E = S::E;
+    constexpr bool kVec = K == 0 && S::PAD == 4;
+    constexpr bool kExch = K > 0 && K + 1 == S::NR;
+    int *bl = lo + RK::addr(q, 0);
+    int *bh = hi + RK::addr(q, 0);
+    if constexpr (kVec) {
+#pragma unroll
+        for (int c = 0; c < E / 4; ++c) {
+            const int4 a = reinterpret_cast<const int4 *>(bl)[c];
+            const int4 b = reinterpret_cast<const int4 *>(bh)[c];
+            v[4 * c] = (long long)(((unsigned long long)(unsigned)b.x << 32) | (unsigned)a.x);
+            v[4 * c + 1] = (long long)(((unsigned long long)(unsigned)b.y << 32) | (unsigned)a.y);
+            v[4 * c + 2] = (long long)(((unsigned long long)(unsigned)b.z << 32) | (unsigned)a.z);
+            v[4 * c + 3] = (long long)(((unsigned long long)(unsigned)b.w << 32) | (unsigned)a.w);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            const int o = RK::addr(0, j);
+            const unsigned a = kExch ? (unsigned)atomicExch(bl + o, 0) : (unsigned)bl[o];
+            const unsigned b = kExch ? (unsigned)atomicExch(bh + o, 0) : (unsigned)bh[o];
+            v[j] = (long long)(((unsigned long long)b << 32) | a);
+        }
+    }
+    reg_fwht<long long, E, RK::nb>(v);
+    if constexpr (K + 1 < S::NR) {
+        if constexpr (kVec) {
+#pragma unroll
+            for (int c = 0; c < E / 4; ++c) {
+                reinterpret_cast<int4 *>(bl)[c] =
+                    make_int4((int)v[4 * c], (int)v[4 * c + 1], (int)v[4 * c + 2], (int)v[4 * c + 3]);
+                reinterpret_cast<int4 *>(bh)[c] =
+                    make_int4((int)(v[4 * c] >> 32), (int)(v[4 * c + 1] >> 32),
+                              (int)(v[4 * c + 2] >> 32), (int)(v[4 * c + 3] >> 32));
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                const int o = RK::addr(0, j);
+                bl[o] = (int)v[j];
+                bh[o] = (int)(v[j] >> 32);
+            }
+        }
+        group_sync<S::P>(g);
+        fx_rounds<L, LE, K + 1>(lo, hi, v, q, g);
+    } else if constexpr (!kExch) {
+        // a single round: zero the words it read
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            const int o = RK::addr(0, j);
+            bl[o] = 0;
+            bh[o] = 0;
+        }
+    }
+}
 
 // ---------------------------------------------------------------- the sketch kernel
 constexpr int kFxThreads = 256;
@@ -193,11 +319,11 @@ constexpr int kFxThreads = 256;
 template <int L>
 struct FxCfg {
     static constexpr int LE = L < 5 ? L : 5;
-    using S = FwhtShape<long long, L, LE>;
+    using S = FwhtShape<float, L, LE>;   // 32-bit word layout of each half array
     static constexpr int E = S::E, P = S::P, G = kFxThreads / P;
     static constexpr bool TM = LE == 5;   // X^ and Z in tensor memory (else registers)
     static constexpr uint32_t COLS = 256; // 4 words per point, 2 threads per TMEM lane
-    static constexpr size_t SMEM = (size_t)G * S::STRIDE * sizeof(long long);
+    static constexpr size_t SMEM = (size_t)2 * G * S::STRIDE * sizeof(int);   // low, high
     static_assert(kFxThreads % P == 0, "CTA must hold whole groups");
     static_assert((size_t)S::N * sizeof(double) <= SMEM, "FP64 reduction must fit");
 };
@@ -234,14 +360,14 @@ sketch_fx64_kernel(const long long *__restrict__ Aq, const long long *__restrict
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int g = tid / P, q = tid % P;
-    long long *sm = reinterpret_cast<long long *>(smem_raw);
-    long long *Sg = sm + g * S::STRIDE;
-    unsigned *S32 = reinterpret_cast<unsigned *>(Sg);
+    int *sm = reinterpret_cast<int *>(smem_raw);
+    int *lo = sm + g * S::STRIDE;              // low halves of the group's slice
+    int *hi = sm + (G + g) * S::STRIDE;        // high halves
 
     if constexpr (Cfg::TM) {
         if (warp == 0) tm::alloc(&s_taddr, Cfg::COLS);
     }
-    for (int i = tid; i < G * S::STRIDE; i += kFxThreads) sm[i] = 0;
+    for (int i = tid; i < 2 * G * S::STRIDE; i += kFxThreads) sm[i] = 0;
     // block scale: S_ref = max over the block's t of 64 - eA_t - eB_t
     int mx = -0x40000000;
     for (int64_t t = t0 + tid; t < t1; t += kFxThreads) mx = max(mx, 64 - expA[t] - expB[t]);
@@ -281,19 +407,22 @@ sketch_fx64_kernel(const long long *__restrict__ Aq, const long long *__restrict
         // A's values carry the block scale 2^(64 - eA - eB - S_ref) <= 1 and
         // 2^-32 (keeps the float-float products and sums in range)
         const int exA = active ? (64 - expA[t] - expB[t] - sref) - 32 : -1000;
-        if (active) scatter_fx<P>(S32, Aq + t * m, tA, m, q);
+        const float sA42 = pow2f(exA + 42), sA21 = pow2f(exA + 21), sA0 = pow2f(exA);
+        if (active) scatter_fx<P>(reinterpret_cast<unsigned *>(lo), hi, Aq + t * m, tA, m, q);
         group_sync<P>(g);
-        fwht_rounds<long long, L, LE, 0>(Sg, v, q, g);
+        fx_rounds<L, LE, 0>(lo, hi, v, q, g);
         if constexpr (Cfg::TM) {
 #pragma unroll
             for (int c = 0; c < E / 16; ++c) {
                 uint32_t hw[16], lw[16];
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    float h, l;
-                    to_ff(v[16 * c + e], exA, h, l);
-                    hw[e] = __float_as_uint(h);
-                    lw[e] = __float_as_uint(l);
+                for (int e = 0; e < 16; e += 2) {
+                    float2 h, l;
+                    to_ff2(v[16 * c + e], v[16 * c + e + 1], sA42, sA21, sA0, h, l);
+                    hw[e] = __float_as_uint(h.x);
+                    hw[e + 1] = __float_as_uint(h.y);
+                    lw[e] = __float_as_uint(l.x);
+                    lw[e + 1] = __float_as_uint(l.y);
                 }
                 tm::st16(tcol + 16 * c, hw);
                 tm::st16(tcol + E + 16 * c, lw);
@@ -303,9 +432,9 @@ sketch_fx64_kernel(const long long *__restrict__ Aq, const long long *__restrict
             for (int j = 0; j < E; ++j) to_ff(v[j], exA, xr[j], xr[E + j]);
         }
         group_sync<P>(g);
-        if (active) scatter_fx<P>(S32, Bq + t * p, tB, p, q);
+        if (active) scatter_fx<P>(reinterpret_cast<unsigned *>(lo), hi, Bq + t * p, tB, p, q);
         group_sync<P>(g);
-        fwht_rounds<long long, L, LE, 0>(Sg, v, q, g);
+        fx_rounds<L, LE, 0>(lo, hi, v, q, g);
         if constexpr (Cfg::TM) {
             tm::wait_st();
 #pragma unroll
@@ -316,13 +445,18 @@ sketch_fx64_kernel(const long long *__restrict__ Aq, const long long *__restrict
                 tm::ld16(tcol + 2 * E + 16 * c, zh);
                 tm::ld16(tcol + 3 * E + 16 * c, zl);
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    float yh, yl;
-                    to_ff(v[16 * c + e], -32, yh, yl);
-                    float a = __uint_as_float(zh[e]), bz = __uint_as_float(zl[e]);
-                    ff_mac(__uint_as_float(hw[e]), __uint_as_float(lw[e]), yh, yl, a, bz);
-                    zh[e] = __float_as_uint(a);
-                    zl[e] = __float_as_uint(bz);
+                for (int e = 0; e < 16; e += 2) {
+                    float2 yh, yl;
+                    to_ff2(v[16 * c + e], v[16 * c + e + 1], 0x1p10f, 0x1p-11f, 0x1p-32f, yh, yl);
+                    float2 za = make_float2(__uint_as_float(zh[e]), __uint_as_float(zh[e + 1]));
+                    float2 zb = make_float2(__uint_as_float(zl[e]), __uint_as_float(zl[e + 1]));
+                    ff_mac2(make_float2(__uint_as_float(hw[e]), __uint_as_float(hw[e + 1])),
+                            make_float2(__uint_as_float(lw[e]), __uint_as_float(lw[e + 1])), yh, yl,
+                            za, zb);
+                    zh[e] = __float_as_uint(za.x);
+                    zh[e + 1] = __float_as_uint(za.y);
+                    zl[e] = __float_as_uint(zb.x);
+                    zl[e + 1] = __float_as_uint(zb.y);
                 }
                 tm::st16(tcol + 2 * E + 16 * c, zh);
                 tm::st16(tcol + 3 * E + 16 * c, zl);
@@ -358,7 +492,7 @@ sketch_fx64_kernel(const long long *__restrict__ Aq, const long long *__restrict
     }
     if constexpr (G == 1) {
 #pragma unroll
-        for (int j = 0; j < E; ++j) out[final_index<long long, L, LE>(q, j)] = zd[j];
+        for (int j = 0; j < E; ++j) out[final_index<float, L, LE>(q, j)] = zd[j];
     } else {
         __syncthreads();
         double *acc = reinterpret_cast<double *>(smem_raw);
@@ -367,7 +501,7 @@ sketch_fx64_kernel(const long long *__restrict__ Aq, const long long *__restrict
         for (int gg = 0; gg < G; ++gg) {
             if (g == gg) {
 #pragma unroll
-                for (int j = 0; j < E; ++j) acc[final_index<long long, L, LE>(q, j)] += zd[j];
+                for (int j = 0; j < E; ++j) acc[final_index<float, L, LE>(q, j)] += zd[j];
             }
             __syncthreads();
         }
@@ -391,7 +525,7 @@ cudaError_t run_fx(const SketchPlan &pl, const long long *Aq, const long long *B
         int64_t gt = (n + 255) / 256;
         if (gt > 152 * 32) gt = 152 * 32;
         if (gt < 1) gt = 1;
-        sketch_table_kernel<long long, L, Cfg::LE><<<(unsigned)gt, 256, 0, s>>>(
+        sketch_table_kernel<float, L, Cfg::LE><<<(unsigned)gt, 256, 0, s>>>(
             hp, d, pl.L, L, pl.C, m, p, tabA, tabB);
         cudaError_t e0 = cudaGetLastError();
         if (e0 != cudaSuccess) return e0;

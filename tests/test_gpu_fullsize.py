@@ -185,3 +185,33 @@ def test_precision_16384_sampled_entries(cmm, precision):
         w = int(g.integers(1 << L16))
         want = orc.R_entry(precision["A64"], precision["B64"], precision["h"].params, L16, r, w)
         assert abs(precision["Ro"][r, w] - want) <= 1e-12 * precision["scale"]
+
+
+def test_planted_8192_fx64_whole_R_and_list(cmm, planted):
+    # the exact fixed-point form at the benchmark configuration: the whole R
+    # within the FP64 tolerance of the oracle's, and its heavy-hitter list
+    # equal to the oracle's outside a band of 1e-9 tau around the threshold
+    A, B, h, Ro = planted["A"], planted["B"], planted["h"], planted["Ro"]
+    R = torch.empty((D8, 1 << L8), dtype=torch.float64, device="cuda")
+    C, (I, J, V) = cmm.multiply_threshold(planted["Ad"], planted["Bd"], h, N8 / 2, capacity=CAP8,
+                                          prec="fx64", R=R)
+    scale = float(np.sum(np.linalg.norm(A, axis=0) * np.linalg.norm(B, axis=1)))
+    assert np.abs(R.cpu().numpy() - Ro).max() <= 1e-12 * scale
+    got = set(zip(I.cpu().tolist(), J.cpu().tolist()))
+    want = set(zip(planted["I"].tolist(), planted["J"].tolist()))   # the oracle's list
+    tau = N8 / 2
+    for (i, j) in got ^ want:
+        e = orc.decompress(Ro, h.params, i, j)
+        assert abs(abs(e) - tau) <= 1e-9 * tau, (i, j, e)
+
+
+def test_precision_16384_fx64_whole_R(cmm, precision):
+    # the precision workload's FP64 copy (the FP32 values widened) through the
+    # exact fixed-point form: the whole R within 1e-12 of sum_t ||A_t|| ||B_t||
+    A = torch.from_numpy(precision["A64"]).cuda()
+    B = torch.from_numpy(precision["B64"]).cuda()
+    R = cmm.sketch(A, B, precision["h"], prec="fx64")
+    err = np.abs(R.cpu().numpy() - precision["Ro"]).max() / precision["scale"]
+    assert err <= 1e-12, err
+    del A, B, R
+    torch.cuda.empty_cache()
