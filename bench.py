@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--log2b", type=int, default=16)
     ap.add_argument("--d", type=int, default=9)
-    ap.add_argument("--prec", default="fx64", choices=["f32", "f64", "fx64", "bf16tc", "f16tc"],
+    ap.add_argument("--prec", default="fx64",
+                    choices=["f32", "f64", "fx64", "ternary", "bf16tc", "f16tc"],
                     help="arithmetic of the timed step (default: the exact fixed-point form, within the FP64 tolerance)")
     ap.add_argument("--compare-steps", type=int, default=3,
                     help="timed steps of each other form (FP32, plain FP64) on the same input")
@@ -134,13 +135,16 @@ def alu_roofline(kernel: str, ops: float, ms: float, note: str = "") -> dict:
 
 
 # the arithmetic each form computes in, and its name
-DTYPE_OF = {"fx64": "int64", "f32": "f32", "f64": "f64", "bf16tc": "bf16", "f16tc": "f16"}
+DTYPE_OF = {"fx64": "int64", "f32": "f32", "f64": "f64", "bf16tc": "bf16", "f16tc": "f16",
+            "ternary": "int16x2"}
 FORM_OF = {"fx64": "exact 64-bit fixed-point butterflies, float-float multiply-accumulate, FP64 "
                    "reduction/inverse/extraction (FP64 tolerance)",
            "f32": "FP32 butterflies (fixed-point scatter), FP64 reduction/inverse/extraction",
            "f64": "plain FP64 butterflies and accumulation",
            "bf16tc": "BF16 tensor-core Hadamard blocks, FP32 accumulation",
-           "f16tc": "FP16 tensor-core Hadamard blocks, FP32 accumulation"}
+           "f16tc": "FP16 tensor-core Hadamard blocks, FP32 accumulation",
+           "ternary": "exact integer form for -1/0/+1 operands: two inner indices per 32-bit word, "
+                      "int32 multiply-accumulate into int64"}
 
 
 def alu_roofline_for(prec: str, kernel: str, ops: float, ms: float) -> dict:
@@ -153,7 +157,10 @@ def alu_roofline_for(prec: str, kernel: str, ops: float, ms: float) -> dict:
     _, _, pk = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
     lanes = SM_COUNT * FP32_LANES_PER_SM * sm_max * 1e6
-    if prec == "fx64":
+    if prec == "ternary":
+        peak, src = lanes * 2 / 1e12, ("152 SMs x 128 integer lanes x %g MHz x 2 (two 16-bit "
+                                       "halves per 32-bit add)" % sm_max)
+    elif prec == "fx64":
         peak, src = lanes / 2 / 1e12, ("152 SMs x 128 integer lanes x %g MHz / 2 instructions "
                                        "per 64-bit add" % sm_max)
     elif prec == "f64":
@@ -474,7 +481,7 @@ def run_cmm(a):
     R_main = R.clone()
     forms = {}
     if not a.no_fp64:
-        for prec in [pr for pr in ("f32", "f64") if pr != a.prec]:
+        for prec in [pr for pr in ("f32", "ternary", "f64") if pr != a.prec]:
             step(prec)
             torch.cuda.synchronize()
             ck = ClockSampler(local)

@@ -64,11 +64,16 @@ typedef enum {
     CMM_PREC_F32 = 1,     /* FP32 butterflies, FP32 accumulation within a block of t */
     CMM_PREC_BF16TC = 2,  /* BF16 operands with exact +-1 Hadamard blocks on the tensor cores, FP32 accumulation */
     CMM_PREC_F16TC = 3,   /* as BF16TC with FP16 operands, scaled to a fixed range (3 more significand bits) */
-    CMM_PREC_FX64 = 4     /* exact 64-bit fixed-point butterflies: each column quantised once to integers
+    CMM_PREC_FX64 = 4,    /* exact 64-bit fixed-point butterflies: each column quantised once to integers
                            * with sum |q| < 2^62 (per-column power of two from its l1 norm), scatter and
                            * transforms exact in int64, float-float multiply-accumulate; R within the
                            * FP64 tolerance (quantisation <= 2^-61 |column|_1 per value).  Operands must
                            * be finite. */
+    CMM_PREC_TERNARY = 5  /* exact integer form for operands whose entries are all -1, 0 or +1 (the
+                           * +-1 inputs of Sec. 5.2): two inner indices per pass as one 32-bit word of
+                           * two 16-bit halves, int32 multiply-accumulate into an int64 sum, R exact.
+                           * Needs log2b >= 14 and m, p < 2^15 (else CMM_ERR_RANGE); any other entry
+                           * gives CMM_ERR_ARG, found by a check that synchronises the stream. */
 } cmm_prec;
 
 /* how the d repetitions are combined */

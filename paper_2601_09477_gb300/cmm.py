@@ -29,13 +29,13 @@ ERR_TIMEOUT = -6
 ERR_WORKSPACE = -8
 
 F64, F32, BF16 = 0, 1, 2
-PREC_F64, PREC_F32, PREC_BF16TC, PREC_F16TC, PREC_FX64 = 0, 1, 2, 3, 4
+PREC_F64, PREC_F32, PREC_BF16TC, PREC_F16TC, PREC_FX64, PREC_TERNARY = 0, 1, 2, 3, 4, 5
 MEDIAN, MEAN = 0, 1
 MAX_D = 64
 MAX_LOG2B = 24
 
 _PREC = {"f64": PREC_F64, "f32": PREC_F32, "bf16tc": PREC_BF16TC, "f16tc": PREC_F16TC,
-         "fx64": PREC_FX64}
+         "fx64": PREC_FX64, "ternary": PREC_TERNARY}
 _REDUCE = {"median": MEDIAN, "mean": MEAN}
 _DTYPE = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}
 

@@ -111,8 +111,8 @@ int cmm_sketch(const void *A, int64_t lda, int32_t transA, const void *B, int64_
     if (rc) return rc;
     rc = check_operands(A, lda, transA, B, ldb, dtype, m, k, p, prec);
     if (rc) return rc;
-    if (prec_tc(prec) && hs->log2b < sketch_bf16_llo())
-        return fail(CMM_ERR_RANGE, "the tensor-core precisions need log2b >= %d", sketch_bf16_llo());
+    rc = check_prec_sizes(prec, hs->log2b, m, p);
+    if (rc) return rc;
     if (!R) return fail(CMM_ERR_ARG, "R is NULL");
     const size_t need = cmm_sketch_workspace_bytes(m, k, p, hs->d, hs->log2b, dtype, prec, transA);
     rc = check_ws(ws, ws_bytes, need);
@@ -196,8 +196,8 @@ int cmm_multiply(const void *A, int64_t lda, int32_t transA, const void *B, int6
     if (rc) return rc;
     rc = check_operands(A, lda, transA, B, ldb, dtype, m, k, p, prec);
     if (rc) return rc;
-    if (prec_tc(prec) && hs->log2b < sketch_bf16_llo())
-        return fail(CMM_ERR_RANGE, "the tensor-core precisions need log2b >= %d", sketch_bf16_llo());
+    rc = check_prec_sizes(prec, hs->log2b, m, p);
+    if (rc) return rc;
     if (reduce != CMM_MEDIAN && reduce != CMM_MEAN) return fail(CMM_ERR_ARG, "bad reduce %d", reduce);
     if (m > 0 && p > 0 && (!C || ldc < p)) return fail(CMM_ERR_ARG, "C is NULL or ldc < p");
     const size_t need = cmm_multiply_workspace_bytes(m, k, p, hs->d, hs->log2b, dtype, prec, transA);
@@ -227,8 +227,8 @@ int cmm_multiply_threshold(const void *A, int64_t lda, int32_t transA, const voi
     if (rc) return rc;
     rc = check_operands(A, lda, transA, B, ldb, dtype, m, k, p, prec);
     if (rc) return rc;
-    if (prec_tc(prec) && hs->log2b < sketch_bf16_llo())
-        return fail(CMM_ERR_RANGE, "the tensor-core precisions need log2b >= %d", sketch_bf16_llo());
+    rc = check_prec_sizes(prec, hs->log2b, m, p);
+    if (rc) return rc;
     if (reduce != CMM_MEDIAN && reduce != CMM_MEAN) return fail(CMM_ERR_ARG, "bad reduce %d", reduce);
     if (m > 0 && p > 0 && (!C || ldc < p)) return fail(CMM_ERR_ARG, "C is NULL or ldc < p");
     const size_t need = cmm_multiply_workspace_bytes(m, k, p, hs->d, hs->log2b, dtype, prec, transA);

@@ -120,9 +120,11 @@ bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int p
     pl.prec = prec;
     pl.L = L;
     const bool fx = prec == CMM_PREC_FX64;   // exact fixed point: FP64 operands, int64 copies
+    const bool tern = prec == CMM_PREC_TERNARY;   // packed pairs of rows, 2^14 slices
     const bool f64 = prec == CMM_PREC_F64 || fx;
     const bool bf16 = prec_tc(prec);
     if (bf16 && L < sketch_bf16_llo()) return false;
+    if (tern && L < kMaxLloF32) return false;
     const int maxLlo = bf16 ? sketch_bf16_llo()
                             : fx ? kMaxLloFx64 : (f64 ? kMaxLloF64 : kMaxLloF32);
     pl.Llo = std::min(L, maxLlo);
@@ -130,13 +132,15 @@ bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int p
     pl.tmem = sketch_tm_supported(prec, pl.Llo) && use_tmem_kernel();
     pl.threads = bf16 ? sketch_bf16_threads()
                  : fx ? sketch_fx64_threads()
+                 : tern ? sketch_i16_threads()
                  : pl.tmem ? sketch_tm_threads()
                            : (f64 ? sketch_threads_f64(pl.Llo) : sketch_threads_f32(pl.Llo));
     pl.smem = bf16 ? sketch_bf16_smem()
               : fx ? sketch_fx64_smem(pl.Llo)
+              : tern ? sketch_i16_smem()
               : pl.tmem ? sketch_tm_smem()
                         : (f64 ? sketch_smem_f64(pl.Llo) : sketch_smem_f32(pl.Llo));
-    const int LE = bf16 ? pl.Llo : pl.tmem ? 7 : std::min(pl.Llo, (f64 && !fx) ? 4 : 5);
+    const int LE = bf16 ? pl.Llo : (pl.tmem || tern) ? 7 : std::min(pl.Llo, (f64 && !fx) ? 4 : 5);
     const int P = (1 << pl.Llo) >> LE;
     const int G = bf16 ? 1 : pl.threads / P;
     const int per_sm = bf16 ? 1 : (pl.tmem || pl.threads < 512) ? 2 : 1;
@@ -148,7 +152,7 @@ bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int p
     // time waves * (t per group + a fixed per-CTA cost of ~2 t for the
     // partial write-out and set-up), preferring fewer blocks on ties
     nparts = std::max(1, std::min(nparts, kMaxParts));
-    if (k < nparts) nparts = 1;
+    if (k < nparts || tern) nparts = 1;   // the ternary form plans in pairs of t, one part
     pl.nparts = nparts;
     pl.nchunks = 0;
     if (ratio > 0.0 && nparts > 1) {
@@ -164,7 +168,8 @@ bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int p
         for (int c = 0; c <= nparts; ++c) pl.kb[c] = k * c / nparts;
     }
     for (int c = 0; c < nparts; ++c) {
-        const int64_t kk = std::max<int64_t>(pl.kb[c + 1] - pl.kb[c], 1);
+        const int64_t kt = pl.kb[c + 1] - pl.kb[c];
+        const int64_t kk = std::max<int64_t>(tern ? (kt + 1) / 2 : kt, 1);
         const int64_t nc_min = std::max<int64_t>(1, (kk + 256 * G - 1) / (256 * G));
         const int64_t nc_max = std::max<int64_t>(nc_min, (kk + G - 1) / G);
         int64_t best = nc_min;
@@ -186,8 +191,8 @@ bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int p
 
     const size_t tb = f64 ? 8 : 4;
     const int tb_dtype = f64 ? CMM_F64 : CMM_F32;
-    pl.prep_A = !(transA && dtype == tb_dtype);
-    pl.prep_B = dtype != tb_dtype;
+    pl.prep_A = !(transA && (dtype == tb_dtype || (tern && dtype == CMM_F64)));
+    pl.prep_B = tern ? dtype == CMM_BF16 : dtype != tb_dtype;   // packing reads FP64 and FP32
     pl.ldat = pl.prep_A ? m : lda;
     pl.ldbp = pl.prep_B ? p : ldb;
     const int64_t b = int64_t(1) << L;
@@ -210,8 +215,30 @@ bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int p
     if (fx) off += align_up((size_t)k * p * sizeof(long long));
     pl.off_exp = off;
     if (fx) off += align_up((size_t)2 * k * sizeof(int));
+    const int64_t pairs = (k + 1) / 2;
+    pl.off_Ap2 = off;
+    if (tern) off += align_up((size_t)pairs * m * sizeof(int));
+    pl.off_Bp2 = off;
+    if (tern) off += align_up((size_t)pairs * p * sizeof(int));
+    pl.off_bad = off;
+    if (tern) off += align_up(sizeof(int));
     pl.total = off;
     return true;
+}
+
+// size limits of the forms whose slices are fixed: the tensor-core forms and
+// the ternary form transform whole slices (log2b at least one slice), and the
+// ternary form's 16-bit halves hold sums of at most m (or p) entries
+int check_prec_sizes(int prec, int log2b, int64_t m, int64_t p) {
+    if (prec_tc(prec) && log2b < sketch_bf16_llo())
+        return fail(CMM_ERR_RANGE, "the tensor-core precisions need log2b >= %d", sketch_bf16_llo());
+    if (prec == CMM_PREC_TERNARY) {
+        if (log2b < kMaxLloF32)
+            return fail(CMM_ERR_RANGE, "the ternary form needs log2b >= %d", kMaxLloF32);
+        if (m >= 32768 || p >= 32768)
+            return fail(CMM_ERR_RANGE, "the ternary form needs m, p < 2^15 (16-bit halves)");
+    }
+    return CMM_OK;
 }
 
 int check_ws(void *ws, size_t ws_bytes, size_t need) {
@@ -229,7 +256,8 @@ int check_operands(const void *A, int64_t lda, int transA, const void *B, int64_
     int rc = check_sizes(m, k, p);
     if (rc) return rc;
     if (!valid_dtype(dtype)) return fail(CMM_ERR_ARG, "bad dtype %d", dtype);
-    if (prec != CMM_PREC_F64 && prec != CMM_PREC_F32 && !prec_tc(prec) && prec != CMM_PREC_FX64)
+    if (prec != CMM_PREC_F64 && prec != CMM_PREC_F32 && !prec_tc(prec) && prec != CMM_PREC_FX64 &&
+        prec != CMM_PREC_TERNARY)
         return fail(CMM_ERR_ARG, "bad precision %d", prec);
     if (transA != 0 && transA != 1) return fail(CMM_ERR_ARG, "transA must be 0 or 1");
     if (m > 0 && k > 0 && !A) return fail(CMM_ERR_ARG, "A is NULL");
@@ -297,7 +325,11 @@ int run_sketch(const void *A, int64_t lda, int transA, const void *B, int64_t ld
     fill_params(hs, hp);
     char *base = static_cast<char *>(ws);
     const size_t es = dtype_size(dtype);
-    const size_t tb = prec == CMM_PREC_F64 ? 8 : 4;
+    // bytes per element of the arrays the sketch reads: the workspace copies
+    // (FP64 for the FP64 and fixed-point forms, else FP32) or the caller's
+    const size_t tb = (prec == CMM_PREC_F64 || prec == CMM_PREC_FX64) ? 8 : 4;
+    const size_t ea = pl.prep_A ? tb : dtype_size(dtype);
+    const size_t eb = pl.prep_B ? tb : dtype_size(dtype);
     const int64_t b = int64_t(1) << hs->log2b;
     char *At = pl.prep_A ? base + pl.off_At : (char *)const_cast<void *>(A);
     char *Bp = pl.prep_B ? base + pl.off_Bp : (char *)const_cast<void *>(B);
@@ -323,7 +355,8 @@ int run_sketch(const void *A, int64_t lda, int transA, const void *B, int64_t ld
         // scatter): A^T rows, then B rows; taken by the preparation kernels
         // where they run, else by a pass over the caller's FP32 rows
         float *cm = colmax + 2 * k0;
-        const bool fx = prec != CMM_PREC_F64 && prec != CMM_PREC_FX64 && kp > 0;
+        const bool fx = prec != CMM_PREC_F64 && prec != CMM_PREC_FX64 &&
+                        prec != CMM_PREC_TERNARY && kp > 0;
         if (fx && (pl.prep_A || pl.prep_B)) {
             e = cudaMemsetAsync(cm, 0, 2 * kp * sizeof(float), s);
             if (e != cudaSuccess) return cuda_fail(e, "column maxima reset");
@@ -342,8 +375,8 @@ int run_sketch(const void *A, int64_t lda, int transA, const void *B, int64_t ld
                               Bp + k0 * pl.ldbp * tb, pl.ldbp, s, fx ? cm + kp : nullptr);
             if (e != cudaSuccess) return cuda_fail(e, "prep B");
         }
-        const char *Atc = At + k0 * pl.ldat * tb;
-        const char *Bpc = Bp + k0 * pl.ldbp * tb;
+        const char *Atc = At + k0 * pl.ldat * ea;
+        const char *Bpc = Bp + k0 * pl.ldbp * eb;
         if (fx && !(pl.prep_A && pl.prep_B)) {
             Span sp("colmax", s, (pl.prep_A || pl.prep_B) ? 1 : 2);
             e = cudaSuccess;
@@ -357,7 +390,33 @@ int run_sketch(const void *A, int64_t lda, int transA, const void *B, int64_t ld
         pp.nchunks = pl.pnch[c];
         double *pc = partial + blk0 * hs->d * b;
         blk0 += pl.pnch[c];
-        if (prec == CMM_PREC_FX64) {
+        if (prec == CMM_PREC_TERNARY) {
+            // pack pairs of rows, check every entry, then sketch (one part)
+            unsigned *Ap2 = reinterpret_cast<unsigned *>(base + pl.off_Ap2);
+            unsigned *Bp2 = reinterpret_cast<unsigned *>(base + pl.off_Bp2);
+            int *bad = reinterpret_cast<int *>(base + pl.off_bad);
+            int hbad = 0;
+            {
+                Span sp("pack_pairs", s, 2);
+                e = cudaMemsetAsync(bad, 0, sizeof(int), s);
+                if (e == cudaSuccess)
+                    e = launch_pack_pairs(Atc, ea == 8, pl.ldat, kp, m, reinterpret_cast<int *>(Ap2),
+                                          bad, s);
+                if (e == cudaSuccess)
+                    e = launch_pack_pairs(Bpc, eb == 8, pl.ldbp, kp, p, reinterpret_cast<int *>(Bp2),
+                                          bad, s);
+            }
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return cuda_fail(e, "ternary packing");
+            if (hbad)
+                return fail(CMM_ERR_ARG, "the ternary form needs every entry of A and B to be -1, 0 or 1");
+            // int32 running sums: each pair adds at most 2 m p in magnitude
+            const double mp2 = 2.0 * (double)std::max<int64_t>(m, 1) * (double)std::max<int64_t>(p, 1);
+            const int flush = (int)std::max(1.0, std::floor(2147483647.0 / mp2));
+            Span sp("sketch_ternary", s, 2);
+            e = launch_sketch_i16(pp, Ap2, Bp2, m, (kp + 1) / 2, p, hs->d, hp, tabA, tabB, flush, pc, s);
+        } else if (prec == CMM_PREC_FX64) {
             // quantise this part's rows of A^T and B to int64 fixed point, then sketch
             long long *Aq = reinterpret_cast<long long *>(base + pl.off_Aq) + k0 * m;
             long long *Bq = reinterpret_cast<long long *>(base + pl.off_Bq) + k0 * p;

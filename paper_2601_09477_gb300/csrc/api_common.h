@@ -68,6 +68,7 @@ size_t dtype_size(int dt);
 int check_sizes(int64_t m, int64_t k, int64_t p);
 bool use_tmem_kernel();
 int check_ws(void *ws, size_t ws_bytes, size_t need);
+int check_prec_sizes(int prec, int log2b, int64_t m, int64_t p);
 int check_operands(const void *A, int64_t lda, int transA, const void *B, int64_t ldb, int dtype,
                    int64_t m, int64_t k, int64_t p, int prec);
 

@@ -133,8 +133,8 @@ int cmm_multiply_host(const void *A, int64_t lda, int32_t transA, const void *B,
     if (rc) return rc;
     rc = check_operands(A, lda, transA, B, ldb, dtype, m, k, p, prec);
     if (rc) return rc;
-    if (prec_tc(prec) && hs->log2b < sketch_bf16_llo())
-        return fail(CMM_ERR_RANGE, "the tensor-core precisions need log2b >= %d", sketch_bf16_llo());
+    rc = check_prec_sizes(prec, hs->log2b, m, p);
+    if (rc) return rc;
     if (reduce != CMM_MEDIAN && reduce != CMM_MEAN) return fail(CMM_ERR_ARG, "bad reduce %d", reduce);
     if (C && ldc < p) return fail(CMM_ERR_ARG, "ldc = %lld < p", (long long)ldc);
     if (count && capacity < 0) return fail(CMM_ERR_ARG, "negative capacity");

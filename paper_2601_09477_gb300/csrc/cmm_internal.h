@@ -61,6 +61,8 @@ struct SketchPlan {
     size_t off_At, off_Bp, off_partial, off_Z, off_tab, off_colmax, total;
     // exact fixed-point form: int64 operands (k x m, k x p) and their row exponents (2k)
     size_t off_Aq, off_Bq, off_exp;
+    // ternary form: packed pairs of rows (ceil(k/2) x m, ceil(k/2) x p words), the check word
+    size_t off_Ap2, off_Bp2, off_bad;
     bool prep_A, prep_B;   // whether A / B are converted into the workspace
     int64_t ldat, ldbp;    // leading dimensions of the operands the sketch reads
     bool tmem;             // use the TMEM variant of the FP32 kernel
@@ -172,6 +174,20 @@ cudaError_t launch_sketch_fx64(const SketchPlan &pl, const long long *Aq, const 
                                int64_t m, int64_t k, int64_t p, int d, const HashParams &hp,
                                tab_t *tabA, tab_t *tabB, const int *expA, const int *expB,
                                double *partial, cudaStream_t s);
+// exact form for ternary operands (CMM_PREC_TERNARY, sketch_i16.cu): rows of X
+// (k x n, FP64 when x_f64 else FP32) packed in pairs, Wp[q][i] = X[2q][i] +
+// 2^16 X[2q+1][i] (ceil(k/2) x n words); *bad |= 1 on an entry other than
+// -1, 0, 1.  The sketch kernel builds its own tables; flush = pairs per int32
+// running sum (2 m p flush < 2^31).
+bool sketch_i16_supported(int Llo);
+int sketch_i16_threads();
+size_t sketch_i16_smem();
+cudaError_t launch_pack_pairs(const void *X, int x_f64, int64_t ldx, int64_t k, int64_t n,
+                              int *Wp, int *bad, cudaStream_t s);
+cudaError_t launch_sketch_i16(const SketchPlan &pl, const unsigned *Ap, const unsigned *Bp,
+                              int64_t m, int64_t npairs, int64_t p, int d, const HashParams &hp,
+                              tab_t *tabA, tab_t *tabB, int flush, double *partial,
+                              cudaStream_t s);
 int sketch_threads_f32(int Llo);
 int sketch_threads_f64(int Llo);
 size_t sketch_smem_f32(int Llo);

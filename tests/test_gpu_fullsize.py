@@ -215,3 +215,15 @@ def test_precision_16384_fx64_whole_R(cmm, precision):
     assert err <= 1e-12, err
     del A, B, R
     torch.cuda.empty_cache()
+
+
+def test_planted_8192_ternary_whole_R_and_list(cmm, planted):
+    # the ternary (packed 16-bit integer) form at the benchmark configuration:
+    # the whole R and the whole heavy-hitter list equal the oracle's bit for bit
+    R = torch.empty((D8, 1 << L8), dtype=torch.float64, device="cuda")
+    C, (I, J, V) = cmm.multiply_threshold(planted["Ad"], planted["Bd"], planted["h"], N8 / 2,
+                                          capacity=CAP8, prec="ternary", R=R)
+    assert np.array_equal(R.cpu().numpy(), planted["Ro"])
+    assert np.array_equal(I.cpu().numpy(), planted["I"])
+    assert np.array_equal(J.cpu().numpy(), planted["J"])
+    assert np.array_equal(V.cpu().numpy(), planted["V"])

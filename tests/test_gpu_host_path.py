@@ -90,3 +90,33 @@ def test_host_path_padded_small(cmm, prec, L):
     R = cmm.sketch(A.cuda(), B.cuda(), h, prec="f32").cpu().numpy()
     scale = float(np.sum(np.linalg.norm(A64, axis=0) * np.linalg.norm(B64, axis=1)))
     assert np.abs(R - Ro).max() / scale <= 1e-5
+
+
+@pytest.mark.parametrize("transA", [False, True])
+def test_host_path_parts_fx64_and_ternary(cmm, transA):
+    # the exact forms through the host path: FP64 operands of 64 MiB, split in
+    # parts along the inner index (the fixed-point form reads its FP64 rows at
+    # 8 bytes per element in every part); N(0,1) operands for the fixed-point
+    # form (within the FP64 tolerance of the device path), +-1 operands for the
+    # ternary form (one part, bit for bit)
+    n = 2048
+    g = np.random.default_rng(3)
+    A = g.standard_normal((n, n))
+    B = g.standard_normal((n, n))
+    h = cmm.make_hashes(19, 5, 15)
+    Ah = torch.from_numpy(np.ascontiguousarray(A.T) if transA else A).pin_memory()
+    Bh = torch.from_numpy(B).pin_memory()
+    Ch, _ = cmm.multiply_host(Ah, Bh, h, prec="fx64", transA=transA)
+    Cd = cmm.multiply(Ah.cuda(), Bh.cuda(), h, prec="fx64", transA=transA)
+    scale = float(np.sum(np.linalg.norm(A, axis=0) * np.linalg.norm(B, axis=1)))
+    assert float((Ch - Cd.cpu()).abs().max()) <= 2e-12 * scale
+    Ro = orc.compress(A, B, h.params, 15, nthreads=orc.max_threads())
+    Co = orc.extract(Ro, h.params, n, n, rows=(100, 104))
+    assert np.abs(Ch[100:104].numpy() - Co).max() <= 2e-12 * scale
+    P = _pm1((n, n), 4)
+    Ph = torch.from_numpy(P).pin_memory()
+    Qh = torch.from_numpy(np.ascontiguousarray(P.T)).pin_memory()
+    Ct, (I, J, V) = cmm.multiply_host(Ph, Qh, h, prec="ternary", tau=0.75 * n, capacity=1 << 20)
+    Ctd = cmm.multiply(Ph.cuda(), Qh.cuda(), h, prec="ternary")
+    assert torch.equal(Ct, Ctd.cpu())
+    assert len(I) > 0 and bool((Ct[I.long(), J.long()] == V).all())

@@ -142,5 +142,5 @@ def test_tensor_core_precisions_checked_before_launch(cmm):
         assert lib.cmm_sketch(dummy, 4, 0, dummy, 4, cmm.F32, 4, 4, 4, small.ref, prec,
                               dummy, dummy, 1 << 30, None) == cmm.ERR_RANGE
         assert "tensor-core" in lib.cmm_last_error().decode()
-    assert lib.cmm_sketch(dummy, 4, 0, dummy, 4, cmm.F32, 4, 4, 4, small.ref, 5,
-                          dummy, dummy, 1 << 30, None) == cmm.ERR_ARG   # no precision 5
+    assert lib.cmm_sketch(dummy, 4, 0, dummy, 4, cmm.F32, 4, 4, 4, small.ref, 6,
+                          dummy, dummy, 1 << 30, None) == cmm.ERR_ARG   # no precision 6
