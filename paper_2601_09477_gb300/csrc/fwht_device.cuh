@@ -83,6 +83,45 @@ __device__ __forceinline__ void reg_fwht(T (&v)[E]) {
     }
 }
 
+// Butterflies over the low NB bits of the register index, two stages at a
+// time where possible: for a, b, c, d at offsets 0, h, 2h, 3h,
+//   a' = (a + b) + (c + d)   b' = (a - b) + (c - d)
+//   c' = (a + b) - (c + d)   d' = (a - b) - (c - d),
+// written as three-operand sums so that each output is one three-input
+// integer add (with carries for 64-bit values): 6 adds for 8 butterfly
+// outputs instead of 8; an odd last stage is a plain radix-2 stage.  For
+// integer T only (exact, or modular for unsigned packed words), where the
+// result equals the stage-by-stage transform.
+template <typename T, int E, int NB>
+__device__ __forceinline__ void reg_fwht_r4(T (&v)[E]) {
+#pragma unroll
+    for (int s = 0; s + 1 < NB; s += 2) {
+        const int h = 1 << s;
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            if ((j & (3 * h)) == 0) {
+                const T a = v[j], b = v[j + h], c = v[j + 2 * h], d = v[j + 3 * h];
+                const T s1 = a + b, d1 = a - b;
+                v[j] = s1 + c + d;
+                v[j + h] = d1 + c - d;
+                v[j + 2 * h] = s1 - c - d;
+                v[j + 3 * h] = d1 - c + d;
+            }
+        }
+    }
+    if constexpr (NB % 2 == 1) {
+        constexpr int h = 1 << (NB - 1);
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            if (!(j & h)) {
+                const T a = v[j], b = v[j + h];
+                v[j] = a + b;
+                v[j + h] = a - b;
+            }
+        }
+    }
+}
+
 // FP32: stage 0 scalar, stages >= 1 on packed pairs (j, j+1) and (j+h, j+h+1);
 // SKIP0 leaves out stage 0 (done by the caller)
 template <int E, int NB, bool SKIP0 = false>

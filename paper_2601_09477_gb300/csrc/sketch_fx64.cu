@@ -281,7 +281,7 @@ __device__ __forceinline__ void fx_rounds(int *lo, int *hi, long long (&v)[1 << 
             v[j] = (long long)(((unsigned long long)b << 32) | a);
         }
     }
-    reg_fwht<long long, E, RK::nb>(v);
+    reg_fwht_r4<long long, E, RK::nb>(v);
     if constexpr (K + 1 < S::NR) {
         if constexpr (kVec) {
 #pragma unroll
@@ -368,6 +368,7 @@ sketch_fx64_kernel(const long long *__restrict__ Aq, const long long *__restrict
         if (warp == 0) tm::alloc(&s_taddr, Cfg::COLS);
     }
     for (int i = tid; i < 2 * G * S::STRIDE; i += kFxThreads) sm[i] = 0;
+
     // block scale: S_ref = max over the block's t of 64 - eA_t - eB_t
     int mx = -0x40000000;
     for (int64_t t = t0 + tid; t < t1; t += kFxThreads) mx = max(mx, 64 - expA[t] - expB[t]);

@@ -43,8 +43,22 @@ static_assert(kIP == 128, "one TMEM lane per thread");
 
 // ---------------------------------------------------------------- packing
 // Wp[q][i] = X[2q][i] + 2^16 X[2q + 1][i] for q < ceil(k / 2) (the second
-// half 0 past the last row); X is k x n (leading dimension ldx) in the
-// butterfly-copy type TI; any entry other than -1, 0, 1 sets *bad.
+// half 0 past the last row); X is k x n (leading dimension ldx), FP64 or FP32;
+// any entry other than -1, 0, 1 sets *bad.  The entries are classified by
+// their bit patterns (integer compares: FP64 compares run at the FP64 rate).
+__device__ __forceinline__ int ternary_of(double x, bool &ok) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
+    ok &= mag == 0ull || mag == 0x3FF0000000000000ull;
+    return mag == 0ull ? 0 : ((b >> 63) ? -1 : 1);
+}
+__device__ __forceinline__ int ternary_of(float x, bool &ok) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned mag = b & 0x7FFFFFFFu;
+    ok &= mag == 0u || mag == 0x3F800000u;
+    return mag == 0u ? 0 : ((b >> 31) ? -1 : 1);
+}
+
 template <typename TI>
 __global__ void pack_pairs_kernel(const TI *__restrict__ X, int64_t ldx, int64_t k, int64_t n,
                                   int *__restrict__ Wp, int *__restrict__ bad) {
@@ -56,10 +70,8 @@ __global__ void pack_pairs_kernel(const TI *__restrict__ X, int64_t ldx, int64_t
         const bool has_b = 2 * q + 1 < k;
         int *out = Wp + q * n;
         for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-            const double a = (double)__ldcs(ra + i);
-            const double b = has_b ? (double)__ldcs(rb + i) : 0.0;
-            ok &= (a == 0.0 || a == 1.0 || a == -1.0) && (b == 0.0 || b == 1.0 || b == -1.0);
-            const int ia = (a == 1.0) - (a == -1.0), ib = (b == 1.0) - (b == -1.0);
+            const int ia = ternary_of(__ldcs(ra + i), ok);
+            const int ib = has_b ? ternary_of(__ldcs(rb + i), ok) : 0;
             out[i] = ia + 65536 * ib;
         }
     }
@@ -178,13 +190,13 @@ __device__ __forceinline__ void i16_fwht(unsigned *S, unsigned (&v)[kIE], int q)
         v[4 * c + 2] = w.z;
         v[4 * c + 3] = w.w;
     }
-    reg_fwht<unsigned, kIE, kILE>(v);
+    reg_fwht_r4<unsigned, kIE, kILE>(v);
 #pragma unroll
     for (int c = 0; c < kIE / 4; ++c) row[c] = make_uint4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < kIE; ++j) v[j] = atomicExch(S + q + 132 * j, 0u);
-    reg_fwht<unsigned, kIE, kILE>(v);
+    reg_fwht_r4<unsigned, kIE, kILE>(v);
 }
 
 // the two halves of a packed word (all arithmetic mod 2^32, unsigned):
