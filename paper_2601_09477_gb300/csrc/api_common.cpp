@@ -131,7 +131,7 @@ bool plan_sketch(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int p
     pl.C = 1 << (L - pl.Llo);
     pl.tmem = sketch_tm_supported(prec, pl.Llo) && use_tmem_kernel();
     pl.threads = bf16 ? sketch_bf16_threads()
-                 : fx ? sketch_fx64_threads()
+                 : fx ? sketch_fx64_threads(pl.Llo)
                  : tern ? sketch_i16_threads()
                  : pl.tmem ? sketch_tm_threads()
                            : (f64 ? sketch_threads_f64(pl.Llo) : sketch_threads_f32(pl.Llo));

@@ -40,7 +40,7 @@ using tab_t = uint16_t;
 // Largest transform slice one CTA holds, per butterfly precision.
 constexpr int kMaxLloF32 = 14;   // 2^14 FP32 = 64 KiB of shared memory
 constexpr int kMaxLloF64 = 13;   // 2^13 FP64 = 64 KiB
-constexpr int kMaxLloFx64 = 13;  // 2^13 int64 = 64 KiB (exact fixed-point form)
+constexpr int kMaxLloFx64 = 14;  // 2^14 int64 = 128 KiB (exact fixed-point form)
 constexpr int kFinishLlo = 12;   // FP64 slice of the inverse transform: 2^12 doubles = 32 KiB
 
 // Most parts a sketch is split into along the inner index (the host-buffer
@@ -166,7 +166,7 @@ cudaError_t launch_finish_fft(const double *partial, int nchunks, int d, int L, 
 // (k x n FP64, leading dimension ldx) quantised to Q (k x n int64) with one
 // power of two 2^expo[t] per row (sum |Q[t][:]| < 2^62); the sketch kernel
 // reads Q and the exponents and builds its own scatter tables (tabA, tabB)
-int sketch_fx64_threads();
+int sketch_fx64_threads(int Llo);
 size_t sketch_fx64_smem(int Llo);
 cudaError_t launch_fx_quantize(const double *X, int64_t ldx, int64_t k, int64_t n, long long *Q,
                                int *expo, cudaStream_t s);

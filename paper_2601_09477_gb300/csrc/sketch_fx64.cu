@@ -24,13 +24,14 @@
 // transform and the extraction are FP64 as in every form.
 //
 // Work decomposition as in the other sketch kernels: one CTA = (repetition r,
-// frequency slice u_hi of 2^13 points, block of t); 256 threads, 32 int64
-// values per thread in three register rounds (5 + 5 + 3 index bits); the
+// frequency slice u_hi of 2^14 points, block of t); 512 threads, 32 int64
+// values per thread in three register rounds (5 + 5 + 4 index bits); the
 // slice's int64 values are two 32-bit arrays in shared memory (low and high
-// halves, 2 x 36 KiB padded, so that the scatter's atomics spread over all 32
-// banks and round 0 reads 16-byte vectors), X^ and the running sum Z
-// as float-float in tensor memory (4 words per point, 256 columns), two CTAs
-// per SM.  Scatter: each int64 is added to shared memory as two 32-bit
+// halves, 2 x 72 KiB padded, so that the scatter's atomics spread over all 32
+// banks and round 0 reads 16-byte vectors), X^ and the running sum Z as
+// float-float in tensor memory (4 words per point, all 512 columns), one CTA
+// per SM.  (Slices of 2^13 with two CTAs of 256 threads per SM scatter every
+// column twice as often: 31.0 against 27.0 ms at n = 8192, b = 2^16, d = 9.)  Scatter: each int64 is added to shared memory as two 32-bit
 // atomics, the low word's carry-out (from the returned old value) added into
 // the high word, which sums the 64-bit values exactly in any order (a 64-bit
 // shared atomic add runs ~6x slower here).
@@ -166,19 +167,33 @@ __device__ __forceinline__ void ff_mac(float xh, float xl, float yh, float yl, f
 // (identical results: each lane is an IEEE operation of its own)
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
-__device__ __forceinline__ float2 chunk_f2(int c0, int c1, float s) {
-    const float2 mf = make_float2(__int_as_float(0x4B400000 + c0), __int_as_float(0x4B400000 + c1));
+// FP32 values with the bit patterns w0, w1 of floats in [2^23, 2^24) (unit
+// in the last place 1), minus `base`, times s: exact for the chunks below
+__device__ __forceinline__ float2 chunk_f2(uint32_t w0, uint32_t w1, float base, float s) {
+    const float2 mf = make_float2(__uint_as_float(w0), __uint_as_float(w1));
     const float2 ss = make_float2(s, s);
-    const float2 k = make_float2(-12582912.f * s, -12582912.f * s);
+    const float2 k = make_float2(-base * s, -base * s);
     return __ffma2_rn(mf, ss, k);
+}
+
+// the chunk bit patterns: the low and middle 21-bit chunks are OR-ed into the
+// mantissa of 2^23 (one logic operation each: 2^23 + c), the signed top chunk
+// (|c2| < 2^20 for |v| < 2^62) is offset by 2^21 (2^23 + 2^21 + c2)
+__device__ __forceinline__ uint32_t top_bits(long long v) {
+    return (uint32_t)((int)(v >> 42) + 0x4B200000);
+}
+__device__ __forceinline__ uint32_t mid_bits(long long v) {
+    return ((uint32_t)((unsigned long long)v >> 21) & 0x1FFFFFu) | 0x4B000000u;
+}
+__device__ __forceinline__ uint32_t low_bits(long long v) {
+    return ((uint32_t)v & 0x1FFFFFu) | 0x4B000000u;
 }
 
 __device__ __forceinline__ void to_ff2(long long v0, long long v1, float s42, float s21,
                                        float s0, float2 &h, float2 &l) {
-    const float2 a = chunk_f2((int)(v0 >> 42), (int)(v1 >> 42), s42);
-    const float2 b = chunk_f2((int)((unsigned long long)v0 >> 21) & 0x1FFFFF,
-                              (int)((unsigned long long)v1 >> 21) & 0x1FFFFF, s21);
-    const float2 c = chunk_f2((int)v0 & 0x1FFFFF, (int)v1 & 0x1FFFFF, s0);
+    const float2 a = chunk_f2(top_bits(v0), top_bits(v1), 10485760.f, s42);   // 2^23 + 2^21
+    const float2 b = chunk_f2(mid_bits(v0), mid_bits(v1), 8388608.f, s21);    // 2^23
+    const float2 c = chunk_f2(low_bits(v0), low_bits(v1), 8388608.f, s0);
     const float2 m1 = make_float2(-1.f, -1.f);
     const float2 sm = __fadd2_rn(a, b);
     const float2 e = __ffma2_rn(__ffma2_rn(a, m1, sm), m1, b);   // b - (s - a)
@@ -314,17 +329,19 @@ __device__ __forceinline__ void fx_rounds(int *lo, int *hi, long long (&v)[1 << 
 }
 
 // ---------------------------------------------------------------- the sketch kernel
-constexpr int kFxThreads = 256;
-
 template <int L>
 struct FxCfg {
+    // 2^14-point slices: one CTA of 512 threads per SM (147 KB of shared
+    // memory, all 512 TMEM columns); smaller slices: 256 threads, 2 CTAs/SM
+    static constexpr int THREADS = L == 14 ? 512 : 256;
+    static constexpr int MINB = THREADS == 512 ? 1 : 2;
     static constexpr int LE = L < 5 ? L : 5;
     using S = FwhtShape<float, L, LE>;   // 32-bit word layout of each half array
-    static constexpr int E = S::E, P = S::P, G = kFxThreads / P;
+    static constexpr int E = S::E, P = S::P, G = THREADS / P;
     static constexpr bool TM = LE == 5;   // X^ and Z in tensor memory (else registers)
-    static constexpr uint32_t COLS = 256; // 4 words per point, 2 threads per TMEM lane
+    static constexpr uint32_t COLS = THREADS / 128 * 128;   // 4 words per point per thread
     static constexpr size_t SMEM = (size_t)2 * G * S::STRIDE * sizeof(int);   // low, high
-    static_assert(kFxThreads % P == 0, "CTA must hold whole groups");
+    static_assert(THREADS % P == 0, "CTA must hold whole groups");
     static_assert((size_t)S::N * sizeof(double) <= SMEM, "FP64 reduction must fit");
 };
 
@@ -332,7 +349,7 @@ struct FxCfg {
 // Aq / Bq: fixed-point operands (k x m, k x p int64), expA / expB their
 // per-row exponents; tables as for the FP32 kernels (int64 word layout).
 template <int L>
-__global__ void __launch_bounds__(kFxThreads, 2)
+__global__ void __launch_bounds__(FxCfg<L>::THREADS, FxCfg<L>::MINB)
 sketch_fx64_kernel(const long long *__restrict__ Aq, const long long *__restrict__ Bq,
                    int64_t m, int64_t k, int64_t p, int Lfull, int C, int64_t chunk, int d,
                    const tab_t *__restrict__ tabA, const tab_t *__restrict__ tabB,
@@ -343,6 +360,7 @@ sketch_fx64_kernel(const long long *__restrict__ Aq, const long long *__restrict
     constexpr int E = Cfg::E, P = Cfg::P, G = Cfg::G, LE = Cfg::LE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint32_t s_taddr;
+    constexpr int kFxThreads = Cfg::THREADS;
     __shared__ int s_red[kFxThreads / 32];
 
     int item = blockIdx.x;
@@ -536,7 +554,7 @@ cudaError_t run_fx(const SketchPlan &pl, const long long *Aq, const long long *B
                                          (int)Cfg::SMEM);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (int64_t)pl.nchunks * d * pl.C;
-    kern<<<(unsigned)blocks, kFxThreads, Cfg::SMEM, s>>>(Aq, Bq, m, k, p, pl.L, pl.C, pl.chunk, d,
+    kern<<<(unsigned)blocks, Cfg::THREADS, Cfg::SMEM, s>>>(Aq, Bq, m, k, p, pl.L, pl.C, pl.chunk, d,
                                                        tabA, tabB, expA, expB, partial);
     return cudaGetLastError();
 }
@@ -547,13 +565,13 @@ cudaError_t run_fx(const SketchPlan &pl, const long long *Aq, const long long *B
 
 namespace cmm {
 
-int sketch_fx64_threads() { return kFxThreads; }
+int sketch_fx64_threads(int Llo) { return Llo == 14 ? FxCfg<14>::THREADS : FxCfg<13>::THREADS; }
 
 size_t sketch_fx64_smem(int Llo) {
     switch (Llo) {
 #define CASE(L) case L: return FxCfg<L>::SMEM;
         CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10)
-        CASE(11) CASE(12) CASE(13)
+        CASE(11) CASE(12) CASE(13) CASE(14)
 #undef CASE
     }
     return 0;
@@ -566,7 +584,7 @@ cudaError_t launch_sketch_fx64(const SketchPlan &pl, const long long *Aq, const 
     switch (pl.Llo) {
 #define CASE(L) case L: return run_fx<L>(pl, Aq, Bq, m, k, p, d, hp, tabA, tabB, expA, expB, partial, s);
         CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8) CASE(9) CASE(10)
-        CASE(11) CASE(12) CASE(13)
+        CASE(11) CASE(12) CASE(13) CASE(14)
 #undef CASE
     }
     return cudaErrorInvalidValue;
