@@ -427,7 +427,14 @@ sketch_fx64_kernel(const long long *__restrict__ Aq, const long long *__restrict
         // 2^-32 (keeps the float-float products and sums in range)
         const int exA = active ? (64 - expA[t] - expB[t] - sref) - 32 : -1000;
         const float sA42 = pow2f(exA + 42), sA21 = pow2f(exA + 21), sA0 = pow2f(exA);
-        if (active) scatter_fx<P, 16>(reinterpret_cast<unsigned *>(lo), hi, Aq + t * m, tA, m, q);
+        if (active) {
+            // 16 elements in flight per thread when every thread has at least
+            // that many, else 8 (a mostly empty batch costs more than it hides)
+            if (m >= 16 * P)
+                scatter_fx<P, 16>(reinterpret_cast<unsigned *>(lo), hi, Aq + t * m, tA, m, q);
+            else
+                scatter_fx<P, 8>(reinterpret_cast<unsigned *>(lo), hi, Aq + t * m, tA, m, q);
+        }
         group_sync<P>(g);
         fx_rounds<L, LE, 0>(lo, hi, v, q, g);
         if constexpr (Cfg::TM) {
@@ -451,7 +458,12 @@ sketch_fx64_kernel(const long long *__restrict__ Aq, const long long *__restrict
             for (int j = 0; j < E; ++j) to_ff(v[j], exA, xr[j], xr[E + j]);
         }
         group_sync<P>(g);
-        if (active) scatter_fx<P, 16>(reinterpret_cast<unsigned *>(lo), hi, Bq + t * p, tB, p, q);
+        if (active) {
+            if (p >= 16 * P)
+                scatter_fx<P, 16>(reinterpret_cast<unsigned *>(lo), hi, Bq + t * p, tB, p, q);
+            else
+                scatter_fx<P, 8>(reinterpret_cast<unsigned *>(lo), hi, Bq + t * p, tB, p, q);
+        }
         group_sync<P>(g);
         fx_rounds<L, LE, 0>(lo, hi, v, q, g);
         if constexpr (Cfg::TM) {
