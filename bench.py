@@ -573,12 +573,22 @@ def run_cmm(a):
                                                 capacity=cap, hh_out=hh, ws=wsh)
         e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / a.e2e_steps, world, dev)
         nhh = int(Ie.numel())
+        # one more call, traced: device time of each copy and kernel span (the copies
+        # run on the library's copy stream, overlapped with the kernels)
+        cmm.trace_enable(True)
+        cmm.multiply_host(Ah, Bh, h, prec=a.prec, out=Ch, tau=tau, capacity=cap, hh_out=hh,
+                          ws=wsh)
+        torch.cuda.synchronize()
+        cmm.trace_enable(False)
+        e2e_spans = {k: round(v[1], 3) for k, v in sorted(cmm.trace_read().items(),
+                                                           key=lambda kv: -kv[1][1])}
         result["e2e"] = {"value": round(e2e_ms, 3), "unit": "ms",
                          "ms_per_problem_whole_job": round(whole_job_ms(e2e_ms, world), 3),
                          "h2d_bytes_per_step": int(2 * n * n * 8),
                          "d2h_bytes_per_step": int(n * n * 8 + nhh * 16),
                          "ms_per_step": round(e2e_ms, 3), "steps": a.e2e_steps,
-                         "api": "cmm_multiply_host (pinned host A, B, C, heavy-hitter list)"}
+                         "api": "cmm_multiply_host (pinned host A, B, C, heavy-hitter list)",
+                         "spans_ms_one_call": e2e_spans}
         del wsh
 
     # FP64 CPU oracle on a bounded sample (rank 0, single GPU only)

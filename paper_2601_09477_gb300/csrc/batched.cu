@@ -129,9 +129,9 @@ __device__ __forceinline__ void sketch_task(const BProblem &pr, const HashRep &H
     const int64_t t1 = (t0 + pr.chunk < pr.k) ? t0 + pr.chunk : pr.k;
     const int64_t b = (int64_t)1 << pr.L;
     double *out = pr.partial + ((int64_t)blk * d + r) * b + (int64_t)u_hi * (1 << L);
-    sketch_block<float, float, L, LE, kBThreads>(pr.At, pr.ldat, pr.Bp, pr.ldbp, pr.m, pr.p, pr.L,
-                                                 u_hi, t0, t1, H, nullptr, nullptr, pr.cm,
-                                                 pr.cm + pr.k, out, smem);
+    sketch_block<float, float, L, LE, kBThreads, true>(pr.At, pr.ldat, pr.Bp, pr.ldbp, pr.m, pr.p,
+                                                       pr.L, u_hi, t0, t1, H, nullptr, nullptr,
+                                                       pr.cm, pr.cm + pr.k, out, smem);
 }
 
 // max |x| over rows [blk * kCmRows, ...) of A^T (rows < k) and B (rows >= k)

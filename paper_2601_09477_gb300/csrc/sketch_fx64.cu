@@ -266,7 +266,8 @@ __device__ __forceinline__ void scatter_fx(unsigned *lo, int *hi, const long lon
 // fwht_device.cuh), leaving the result in v (last-round layout) and the
 // arrays zeroed for the next scatter.  Round 0 reads its contiguous rows as
 // 16-byte vectors; the last round (of two or more) reads each word and zeroes
-// it by one exchange, so no clearing pass is needed.
+// it by one exchange, so no clearing pass is needed, and ends with the
+// group's barrier before its butterflies (the arrays are free from there on).
 template <int L, int LE, int K>
 __device__ __forceinline__ void fx_rounds(int *lo, int *hi, long long (&v)[1 << LE], int q,
                                           int g) {
@@ -295,6 +296,9 @@ __device__ __forceinline__ void fx_rounds(int *lo, int *hi, long long (&v)[1 << 
             const unsigned b = kExch ? (unsigned)atomicExch(bh + o, 0) : (unsigned)bh[o];
             v[j] = (long long)(((unsigned long long)b << 32) | a);
         }
+        // every read of the slice is done: the group's next scatter may start
+        // while this round's butterflies and the caller's conversion run
+        if constexpr (kExch) group_sync<S::P>(g);
     }
     reg_fwht_r4<long long, E, RK::nb>(v);
     if constexpr (K + 1 < S::NR) {
@@ -457,7 +461,7 @@ sketch_fx64_kernel(const long long *__restrict__ Aq, const long long *__restrict
 #pragma unroll
             for (int j = 0; j < E; ++j) to_ff(v[j], exA, xr[j], xr[E + j]);
         }
-        group_sync<P>(g);
+        if constexpr (S::NR < 2) group_sync<P>(g);   // else synchronised in the last round
         if (active) {
             if (p >= 16 * P)
                 scatter_fx<P, 16>(reinterpret_cast<unsigned *>(lo), hi, Bq + t * p, tB, p, q);
@@ -501,7 +505,7 @@ sketch_fx64_kernel(const long long *__restrict__ Aq, const long long *__restrict
                 ff_mac(xr[j], xr[E + j], yh, yl, zr[j], zr[E + j]);
             }
         }
-        group_sync<P>(g);
+        if constexpr (S::NR < 2) group_sync<P>(g);
     }
 
     // the block's Z = (zh + zl) 2^S_ref in FP64

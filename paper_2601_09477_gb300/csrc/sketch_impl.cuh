@@ -253,7 +253,15 @@ __device__ __forceinline__ void scatter_table_fixed(int *Sg, const float *__rest
 // [t0, t1); writes its FP64 partial Z slice to `out` (N values).  cmA[t] and
 // cmB[t] are the column maxima of A^T[t] and B[t] (FP32 butterflies only).
 // smem_raw must hold sketch_smem_bytes<L, LE, THREADS, T>() bytes.
-template <typename T, typename TZ, int L, int LE, int THREADS>
+// L2 prefetch of the 128-byte line holding p (no fault, no result)
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// PF: while a group works on inner index t, its threads prefetch the rows
+// A^T[t + G] and B[t + G] it takes next into the L2 (for callers whose
+// operands are not already there, such as the batched kernel's sketch tasks)
+template <typename T, typename TZ, int L, int LE, int THREADS, bool PF = false>
 __device__ __forceinline__ void sketch_block(const T *__restrict__ At, int64_t ldat,
                                              const T *__restrict__ Bp, int64_t ldbp, int64_t m,
                                              int64_t p, int Lfull, uint32_t u_hi, int64_t t0,
@@ -295,6 +303,16 @@ __device__ __forceinline__ void sketch_block(const T *__restrict__ At, int64_t l
     for (int64_t it = 0; it < iters; ++it) {
         const int64_t t = t0 + it * G + g;
         const bool active = t < t1;
+        if constexpr (PF) {
+            if (t + G < t1) {
+                const char *na = reinterpret_cast<const char *>(At + (t + G) * ldat);
+                const char *nb = reinterpret_cast<const char *>(Bp + (t + G) * ldbp);
+                for (int64_t o = (int64_t)q * 128; o < m * (int64_t)sizeof(T); o += (int64_t)P * 128)
+                    prefetch_l2(na + o);
+                for (int64_t o = (int64_t)q * 128; o < p * (int64_t)sizeof(T); o += (int64_t)P * 128)
+                    prefetch_l2(nb + o);
+            }
+        }
         float sA = 1.f, invA = 1.f, sB = 1.f, invB = 1.f;
         if constexpr (FX) {
             if (active) {
