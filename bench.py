@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--no-dgemm", action="store_true", help="skip the cuBLAS DGEMM comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--workload", default="planted",
                     choices=["planted", "batched", "precision", "diff", "cyclic", "paper",
                              "instances"],
@@ -562,16 +562,20 @@ def run_cmm(a):
         wsh = torch.empty(cmm.multiply_host_workspace_bytes(n, n, n, h, torch.float64, a.prec,
                                                             capacity=cap),
                           dtype=torch.uint8, device=dev)
-        for _ in range(2):
+        for _ in range(max(3, a.warmup)):
             cmm.multiply_host(Ah, Bh, h, prec=a.prec, out=Ch, tau=tau, capacity=cap,
                               hh_out=hh, ws=wsh)
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
+        calls = []
         for _ in range(a.e2e_steps):
+            c0 = time.perf_counter()
             _, (Ie, Je, Ve) = cmm.multiply_host(Ah, Bh, h, prec=a.prec, out=Ch, tau=tau,
                                                 capacity=cap, hh_out=hh, ws=wsh)
+            calls.append((time.perf_counter() - c0) * 1e3)
         e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / a.e2e_steps, world, dev)
+        calls.sort()
         nhh = int(Ie.numel())
         # one more call, traced: device time of each copy and kernel span (the copies
         # run on the library's copy stream, overlapped with the kernels)
@@ -587,6 +591,8 @@ def run_cmm(a):
                          "h2d_bytes_per_step": int(2 * n * n * 8),
                          "d2h_bytes_per_step": int(n * n * 8 + nhh * 16),
                          "ms_per_step": round(e2e_ms, 3), "steps": a.e2e_steps,
+                         "call_ms_min": round(calls[0], 3),
+                         "call_ms_median": round(calls[len(calls) // 2], 3),
                          "api": "cmm_multiply_host (pinned host A, B, C, heavy-hitter list)",
                          "spans_ms_one_call": e2e_spans}
         del wsh
