@@ -16,7 +16,7 @@ import torch
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 1e-5}
+TOL = {"f64": 1e-12, "fx64": 1e-12, "f32": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -47,7 +47,7 @@ def _scale(A, B):
     return float(np.sum(np.linalg.norm(A, axis=0) * np.linalg.norm(B, axis=1)))
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "fx64", "f32"])
 def test_noalloc_matches_workspace_version_twice(cmm, prec):
     from oracle import oracle as orc
     g = np.random.default_rng(12)
