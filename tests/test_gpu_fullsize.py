@@ -227,3 +227,45 @@ def test_planted_8192_ternary_whole_R_and_list(cmm, planted):
     assert np.array_equal(I.cpu().numpy(), planted["I"])
     assert np.array_equal(J.cpu().numpy(), planted["J"])
     assert np.array_equal(V.cpu().numpy(), planted["V"])
+
+
+# ---------------------------------------------------------------- m = p = 2^16
+def test_max_size_65536_squared(cmm):
+    # 2^32 estimates (every linear index i p + j beyond 2^31 from row 32768 on,
+    # a 32 GiB estimate): the whole R of the exact fixed-point form against the
+    # oracle's (FP64 tolerance), rows of C at the start, the middle and the end
+    # bit for bit against the oracle's Decompress of the same R, and the whole
+    # heavy-hitter list straight from R against the oracle's list bit for bit.
+    # A short inner dimension keeps the operands small; four planted products
+    # (two beyond the 2^31-th entry) stand out of the sketch noise.
+    n, k, L, d = 65536, 48, 14, 3
+    g = np.random.default_rng(65536)
+    A = g.standard_normal((n, k))
+    B = g.standard_normal((k, n))
+    spikes = [(5, 7, 0), (40000, 65535, 1), (65535, 40001, 2), (31000, 33000, 3)]
+    for (i, j, t) in spikes:
+        A[i, t] = 316.0
+        B[t, j] = 316.0
+    h = cmm.make_hashes(65536, d, L)
+    Ad = torch.from_numpy(A).cuda()
+    Bd = torch.from_numpy(B).cuda()
+    R = torch.empty((d, 1 << L), dtype=torch.float64, device="cuda")
+    C = cmm.multiply(Ad, Bd, h, prec="fx64", R=R)
+    Rn = R.cpu().numpy()
+    Ro = orc.compress(A, B, h.params, L, nthreads=orc.max_threads())
+    scale = float(np.sum(np.linalg.norm(A, axis=0) * np.linalg.norm(B, axis=1)))
+    assert np.abs(Rn - Ro).max() <= 1e-12 * scale
+    for i0 in (0, 32767, 32768, 65534):
+        rows = C[i0:i0 + 2].cpu().numpy()
+        assert np.array_equal(rows, orc.extract(Rn, h.params, n, n, rows=(i0, i0 + 2)))
+    del C
+    torch.cuda.empty_cache()
+    tau = 2.5e4
+    I, J, V = cmm.heavy_hitters(R, h, n, n, tau, capacity=1 << 16)
+    Io, Jo, Vo = orc.heavy_hitters(Rn, h.params, n, n, tau, capacity=1 << 16,
+                                   nthreads=orc.max_threads())
+    assert len(Io) >= len(spikes)
+    assert np.array_equal(I.cpu().numpy(), Io)
+    assert np.array_equal(J.cpu().numpy(), Jo)
+    assert np.array_equal(V.cpu().numpy(), Vo)
+    assert {(i, j) for (i, j, _) in spikes} <= set(zip(Io.tolist(), Jo.tolist()))
