@@ -113,7 +113,8 @@ def source_hash(prec: str = "f32"):
     h = hashlib.sha256()
     names = (["sketch_fx64.cu", "fwht_device.cuh", "tmem_device.cuh", "sketch_impl.cuh"]
              if prec == "fx64" else
-             ["sketch_impl.cuh", "fwht_device.cuh", "sketch_f32.cu", "sketch_tm.cu"])
+             ["sketch_impl.cuh", "fwht_device.cuh", "sketch_f32.cu", "sketch_tm.cu",
+              "tm_slice.cuh"])
     for name in names:
         with open(os.path.join(ROOT, "paper_2601_09477_gb300", "csrc", name), "rb") as f:
             h.update(f.read())

@@ -36,10 +36,20 @@ bool plan_adjoint(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int 
     const size_t es = f64 ? 8 : 4;
     const int pad = (!f64 && LE == 5) ? 4 : 1;   // shared-memory pad words per row
     pl.smem = (size_t)G * ((size_t)N + (size_t)pad * (N >> LE) + m + p) * es;
+    int64_t slots = num_sms();
+    int Gt = G;
+    if (!f64 && pl.Llo == adjoint_tm_llo() && adjoint_tm_smem(m, p) <= kMaxDynSmem) {
+        // the tensor-memory kernel: 128 threads, two CTAs per SM when their
+        // shared memory allows
+        pl.tm = true;
+        pl.threads = adjoint_tm_threads();
+        pl.smem = adjoint_tm_smem(m, p);
+        Gt = 1;
+        if (2 * pl.smem <= kMaxDynSmem) slots *= 2;
+    }
     if (pl.smem > kMaxDynSmem) return false;
-    const int64_t slots = num_sms();
     const int64_t kk = std::max<int64_t>(k, 1);
-    const int64_t nc_max = std::max<int64_t>(1, (kk + G - 1) / G);
+    const int64_t nc_max = std::max<int64_t>(1, (kk + Gt - 1) / Gt);
     int64_t best = 1;
     double best_eff = -1.0;
     for (int64_t nc = 1; nc <= std::min<int64_t>(nc_max, 8 * slots); ++nc) {
@@ -76,6 +86,14 @@ bool plan_adjoint(int64_t m, int64_t k, int64_t p, int d, int L, int dtype, int 
     off += align_up((size_t)k * p * es);
     pl.off_colmax = off;
     if (!f64) off += align_up((size_t)2 * k * sizeof(float));
+    if (pl.tm) {
+        pl.off_tabA = off;
+        off += align_up((size_t)d * pl.C * m * sizeof(tab_t));
+        pl.off_tabB = off;
+        off += align_up((size_t)d * pl.C * p * sizeof(tab_t));
+        pl.off_Gs32 = off;
+        off += align_up((size_t)d * ((size_t)1 << L) * sizeof(float));
+    }
     pl.total = off;
     return true;
 }
@@ -168,8 +186,15 @@ int cmm_backward(const void *A, int64_t lda, int32_t transA, const void *B, int6
         if (e != cudaSuccess) return cuda_fail(e, "column maxima");
     }
     {
-        Span sp(prec == CMM_PREC_F64 ? "adjoint_f64" : "adjoint_f32", s);
-        e = launch_adjoint(pl, At, Bp, m, k, p, hs->d, hp, Gs, colmax, dAt, dBt, s);
+        Span sp(prec == CMM_PREC_F64 ? "adjoint_f64" : "adjoint_f32", s, pl.tm ? 3 : 1);
+        if (pl.tm)
+            e = launch_adjoint_tm(pl, (const float *)At, (const float *)Bp, m, k, p, hs->d, hp,
+                                  Gs, reinterpret_cast<float *>(base + pl.off_Gs32),
+                                  reinterpret_cast<tab_t *>(base + pl.off_tabA),
+                                  reinterpret_cast<tab_t *>(base + pl.off_tabB), colmax,
+                                  (float *)dAt, (float *)dBt, s);
+        else
+            e = launch_adjoint(pl, At, Bp, m, k, p, hs->d, hp, Gs, colmax, dAt, dBt, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "adjoint kernel");
     {

@@ -84,6 +84,10 @@ struct AdjointPlan {
     bool prep_A, prep_B;
     int64_t ldat, ldbp;
     size_t off_At, off_Bp, off_G, off_Gs, off_Z, off_dAt, off_dBt, off_colmax, total;
+    // FP32 with 2^14-point slices: the tensor-memory kernel (adjoint_tm.cu),
+    // with the sketch's packed tables and an FP32 copy of Gs
+    bool tm = false;
+    size_t off_tabA = 0, off_tabB = 0, off_Gs32 = 0;
 };
 
 int adjoint_threads(int prec, int Llo);
@@ -93,6 +97,13 @@ cudaError_t launch_adj_g(const HashParams &hp, int d, int L, int64_t P, const in
 cudaError_t launch_adjoint(const AdjointPlan &pl, const void *At, const void *Bp, int64_t m,
                            int64_t k, int64_t p, int d, const HashParams &hp, const double *Gs,
                            const float *colmax, void *dAt, void *dBt, cudaStream_t s);
+int adjoint_tm_threads();
+int adjoint_tm_llo();
+size_t adjoint_tm_smem(int64_t m, int64_t p);
+cudaError_t launch_adjoint_tm(const AdjointPlan &pl, const float *At, const float *Bp, int64_t m,
+                              int64_t k, int64_t p, int d, const HashParams &hp, const double *Gs,
+                              float *Gs32, tab_t *tabA, tab_t *tabB, const float *colmax,
+                              float *dAt, float *dBt, cudaStream_t s);
 // dst (dst_dtype, leading dimension ldd) = src (rows x cols, FP64 when src_f64
 // else FP32, contiguous), transposed when `transpose`
 cudaError_t launch_convert_out(const void *src, int src_f64, int64_t rows, int64_t cols,

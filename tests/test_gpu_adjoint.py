@@ -27,7 +27,8 @@ def _dev(x, dtype=torch.float64):
 
 
 @pytest.mark.parametrize("shape", [(64, 50, 70, 8, 3), (200, 130, 90, 12, 5),
-                                   (300, 64, 257, 15, 3), (33, 17, 40, 3, 2)])
+                                   (300, 64, 257, 15, 3), (33, 17, 40, 3, 2),
+                                   (512, 96, 256, 14, 4), (1000, 40, 3000, 17, 2)])
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("transA", [False, True])
 def test_backward_matches_oracle(cmm, shape, prec, transA):
