@@ -126,53 +126,66 @@ adjoint_tm_kernel(const float *__restrict__ At, int64_t ldat, const float *__res
 
     float v[kTmE];
     for (int64_t t = t0; t < t1; ++t) {
+        if (t + 1 < t1) {   // this CTA's next rows, into the L2 (no other CTA reads them)
+            const char *na = reinterpret_cast<const char *>(At + (t + 1) * ldat);
+            const char *nb = reinterpret_cast<const char *>(Bp + (t + 1) * ldbp);
+            for (int64_t o = (int64_t)q * 128; o < m * 4; o += (int64_t)kTmP * 128) prefetch_l2(na + o);
+            for (int64_t o = (int64_t)q * 128; o < p * 4; o += (int64_t)kTmP * 128) prefetch_l2(nb + o);
+        }
         for (int64_t x = q; x < m; x += kTmP) dAc[x] = 0.f;
         for (int64_t x = q; x < p; x += kTmP) dBr[x] = 0.f;
         for (int r = 0; r < d; ++r) {
             const int64_t slot = (int64_t)r * C + u_hi;
-            const tab_t *tA = tabA + slot * m;
-            const tab_t *tB = tabB + slot * p;
             const float *gr = Gs32 + (int64_t)r * b + (int64_t)u_hi * (1 << kTmL);
-            // H x_t into tensor memory
-            float sc, inv;
-            fixed_scale(__ldg(colmax + t), s_cmax[r], sc, inv);
-            if (vec4)
-                scatter_fixed_v4<16>(Si, At + t * ldat, tA, m, q, sc);
-            else
-                scatter_fixed<32>(Si, At + t * ldat, tA, m, q, sc);
-            __syncthreads();
-            tm_fwht(S, v, q, inv);
+            // half 0: H x_t into tensor memory; half 1: H y_t stays in v.  The
+            // halves (and below, the two gradients) share one copy of the code:
+            // the unrolled transforms would not fit the instruction cache twice.
+#pragma unroll 1
+            for (int half = 0; half < 2; ++half) {
+                float sc, inv;
+                fixed_scale(__ldg(colmax + (half ? k : 0) + t), s_cmax[half * CMM_MAX_D + r], sc,
+                            inv);
+                const float *col = half ? Bp + t * ldbp : At + t * ldat;
+                const tab_t *tab = half ? tabB + slot * p : tabA + slot * m;
+                const int64_t n = half ? p : m;
+                if (vec4)
+                    scatter_fixed_v4<16>(Si, col, tab, n, q, sc);
+                else
+                    scatter_fixed<32>(Si, col, tab, n, q, sc);
+                __syncthreads();
+                tm_fwht(S, v, q, inv);
+                if (half == 0) {
 #pragma unroll
-            for (int c = 0; c < kTmE / 16; ++c) tmem_st16_nowait(tx + 16 * c, v + 16 * c);
-            __syncthreads();   // every thread's exchange of the slice done before the next scatter
-            // H y_t in registers
-            fixed_scale(__ldg(colmax + k + t), s_cmax[CMM_MAX_D + r], sc, inv);
-            if (vec4)
-                scatter_fixed_v4<16>(Si, Bp + t * ldbp, tB, p, q, sc);
-            else
-                scatter_fixed<32>(Si, Bp + t * ldbp, tB, p, q, sc);
-            __syncthreads();
-            tm_fwht(S, v, q, inv);
-            // dA: H (Gs o H y), gathered at the rows' buckets
-#pragma unroll
-            for (int j = 0; j < kTmE; ++j) v[j] *= __ldg(gr + q + 128 * j);
-            back_fwht_to_smem(S, v, q);
-            __syncthreads();
-            gather_tab(S, dAc, tA, m, q);
-            __syncthreads();
-            // dB: H (Gs o H x), gathered at the columns' buckets
-            tmem_wait_st();
-#pragma unroll
-            for (int c = 0; c < kTmE / 16; ++c) {
-                float xs[16];
-                tmem_ld16(tx + 16 * c, xs);
-#pragma unroll
-                for (int e = 0; e < 16; ++e) v[16 * c + e] = xs[e] * __ldg(gr + q + 128 * (16 * c + e));
+                    for (int c = 0; c < kTmE / 16; ++c) tmem_st16_nowait(tx + 16 * c, v + 16 * c);
+                    __syncthreads();   // every thread's exchange of the slice done before the next scatter
+                }
             }
-            back_fwht_to_smem(S, v, q);
-            __syncthreads();
-            gather_tab(S, dBr, tB, p, q);
-            __syncthreads();
+            // grad 0: dA = H (Gs o H y) gathered at the rows' buckets;
+            // grad 1: dB = H (Gs o H x) gathered at the columns' buckets
+#pragma unroll 1
+            for (int grad = 0; grad < 2; ++grad) {
+                if (grad == 0) {
+#pragma unroll
+                    for (int j = 0; j < kTmE; ++j) v[j] *= __ldg(gr + q + 128 * j);
+                } else {
+                    tmem_wait_st();
+#pragma unroll
+                    for (int c = 0; c < kTmE / 16; ++c) {
+                        float xs[16];
+                        tmem_ld16(tx + 16 * c, xs);
+#pragma unroll
+                        for (int e = 0; e < 16; ++e)
+                            v[16 * c + e] = xs[e] * __ldg(gr + q + 128 * (16 * c + e));
+                    }
+                }
+                back_fwht_to_smem(S, v, q);
+                __syncthreads();
+                if (grad == 0)
+                    gather_tab(S, dAc, tabA + slot * m, m, q);
+                else
+                    gather_tab(S, dBr, tabB + slot * p, p, q);
+                __syncthreads();
+            }
             // the slice zero again for the next scatter (pad words are never written)
             {
                 float4 *row = reinterpret_cast<float4 *>(S + 132 * q);
