@@ -215,20 +215,38 @@ __device__ __forceinline__ void ff_mac2(float2 xh, float2 xl, float2 yh, float2 
     zh = sm;
 }
 
-// 64-bit add of v into word `idx` of the slice, held as two 32-bit arrays
-// (low and high halves), by two 32-bit atomics: the low word's carry-out,
-// read from the old value it returns, goes into the high word with v's high
-// half; the final 64-bit value is the exact sum in any order
-__device__ __forceinline__ void add64_shared(unsigned *lo, int *hi, uint32_t idx, long long v) {
-    const unsigned l = (unsigned)v;
-    const unsigned old = atomicAdd(lo + idx, l);
-    const int h = (int)(v >> 32) + ((old + l) < old ? 1 : 0);
-    if (h != 0) atomicAdd(hi + idx, h);
+// scatter one fixed-point column (n int64 values) with the packed table
+// (padded word of the bucket in bits 0-14, sign in bit 15).  Each int64 is
+// added to the slice (two 32-bit arrays, low and high halves) by two 32-bit
+// atomics: the low word's carry-out, read from the old value it returns, goes
+// into the high word with the value's high half, so the 64-bit sums are exact
+// in any order.  Batches of B values per thread: all loads first, then the
+// low-word atomics of four values at a time (their round trips overlap;
+// eight at a time spill registers), then those values' high words.
+template <int P, int B = 8>
+__device__ __forceinline__ void scatter_batch(unsigned *lo, int *hi, const long long (&v)[B],
+                                              const tab_t (&w)[B], int cnt) {
+    constexpr int H = B < 4 ? B : 4;   // low-word atomics in flight at once
+#pragma unroll
+    for (int e0 = 0; e0 < B; e0 += H) {
+        unsigned old[H];
+#pragma unroll
+        for (int e = 0; e < H; ++e) {
+            const long long s = (w[e0 + e] >> 15) ? -v[e0 + e] : v[e0 + e];
+            if (e0 + e < cnt) old[e] = atomicAdd(lo + (w[e0 + e] & 0x7fffu), (unsigned)s);
+        }
+#pragma unroll
+        for (int e = 0; e < H; ++e) {
+            if (e0 + e < cnt) {
+                const long long s = (w[e0 + e] >> 15) ? -v[e0 + e] : v[e0 + e];
+                const unsigned l = (unsigned)s;
+                const int h = (int)(s >> 32) + ((old[e] + l) < old[e] ? 1 : 0);
+                if (h != 0) atomicAdd(hi + (w[e0 + e] & 0x7fffu), h);
+            }
+        }
+    }
 }
 
-// scatter one fixed-point column (n int64 values) with the packed table
-// (padded word of the bucket in bits 0-14, sign in bit 15); batches of
-// B values per thread with all loads first
 template <int P, int B = 8>
 __device__ __forceinline__ void scatter_fx(unsigned *lo, int *hi, const long long *__restrict__ col,
                                            const tab_t *__restrict__ tab, int64_t n, int q) {
@@ -241,8 +259,7 @@ __device__ __forceinline__ void scatter_fx(unsigned *lo, int *hi, const long lon
             v[e] = __ldcs(col + i + e * (int64_t)P);
             w[e] = __ldg(tab + i + e * (int64_t)P);
         }
-#pragma unroll
-        for (int e = 0; e < B; ++e) add64_shared(lo, hi, w[e] & 0x7fffu, (w[e] >> 15) ? -v[e] : v[e]);
+        scatter_batch<P, B>(lo, hi, v, w, B);
     }
     if (i < n) {
         long long v[B];
@@ -253,10 +270,8 @@ __device__ __forceinline__ void scatter_fx(unsigned *lo, int *hi, const long lon
             v[e] = ok ? __ldcs(col + i + e * (int64_t)P) : 0ll;
             w[e] = ok ? __ldg(tab + i + e * (int64_t)P) : (tab_t)0;
         }
-#pragma unroll
-        for (int e = 0; e < B; ++e)
-            if (i + e * (int64_t)P < n)
-                add64_shared(lo, hi, w[e] & 0x7fffu, (w[e] >> 15) ? -v[e] : v[e]);
+        // the elements of the last batch are the first (n - i + P - 1) / P of it
+        scatter_batch<P, B>(lo, hi, v, w, (int)((n - i + P - 1) / P));
     }
 }
 
