@@ -490,10 +490,8 @@ sketch_fx64_kernel(const long long *__restrict__ Aq, const long long *__restrict
 #pragma unroll
             for (int c = 0; c < E / 16; ++c) {
                 uint32_t hw[16], lw[16], zh[16], zl[16];
-                tm::ld16(tcol + 16 * c, hw);
-                tm::ld16(tcol + E + 16 * c, lw);
-                tm::ld16(tcol + 2 * E + 16 * c, zh);
-                tm::ld16(tcol + 3 * E + 16 * c, zl);
+                tm::ld16x4(tcol + 16 * c, hw, tcol + E + 16 * c, lw, tcol + 2 * E + 16 * c, zh,
+                           tcol + 3 * E + 16 * c, zl);
 #pragma unroll
                 for (int e = 0; e < 16; e += 2) {
                     float2 yh, yl;
