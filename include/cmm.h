@@ -67,7 +67,7 @@ typedef enum {
     CMM_PREC_FX64 = 4,    /* exact 64-bit fixed-point butterflies: each column quantised once to integers
                            * with sum |q| < 2^62 (per-column power of two from its l1 norm), scatter and
                            * transforms exact in int64, float-float multiply-accumulate; R within the
-                           * FP64 tolerance (quantisation <= 2^-61 |column|_1 per value).  Operands must
+                           * FP64 tolerance (quantisation <= 2^-60 |column|_1 per value).  Operands must
                            * be finite. */
     CMM_PREC_TERNARY = 5  /* exact integer form for operands whose entries are all -1, 0 or +1 (the
                            * +-1 inputs of Sec. 5.2): two inner indices per pass as one 32-bit word of

@@ -10,9 +10,10 @@
 // then an exact integer of magnitude below 2^62 (|H f|_inf <= |f|_1 <= sum_i
 // |q_i|), so the scatter and all butterflies are exact int64 arithmetic and
 // independent of the order of the atomics.  The only rounding before the
-// multiply is the quantisation, |a_i - q_i 2^-e| <= 2^-(e+1) <= 2^-61 |a|_1,
-// which moves R_r[w] by at most 2^-61 c_max (|A_t|_1 |B_t|_1 + ...) per t --
-// about 2^-45 of sum_t |A_t|_2 |B_t|_2 at m = p = 8192 in the worst case.
+// multiply is the quantisation, |a_i - q_i 2^-e| <= 2^-(e+1) <= 2^-61 |a|_1
+// (2^-60 |a|_1 when |a|_1 lies just below a power of two, see the bound
+// below), which moves R_r[w] by at most 2^-60 c_max (|A_t|_1 |B_t|_1 + ...)
+// per t -- about 2^-44 of sum_t |A_t|_2 |B_t|_2 at m = p = 8192 in the worst case.
 //
 // Multiply-accumulate.  Each transformed value X^ (int64) is split into three
 // 21-bit chunks that convert to FP32 exactly (a magic-number add, no
@@ -46,9 +47,17 @@ namespace {
 
 // ---------------------------------------------------------------- quantisation
 // One CTA per row t of X (k rows of n FP64 values, leading dimension ldx):
-// l1 = sum |X[t][:]| (fixed reduction order: deterministic), e[t] = 61 -
-// (exponent of l1, so that l1 < 2^E), clamped to [-1022, 1023], and
-// Q[t][i] = round(X[t][i] 2^e) (int64, leading dimension n).
+// an upper bound U of l1 = sum |X[t][:]|, e[t] = 61 - E with U < 2^E, clamped
+// to [-1022, 1023], and Q[t][i] = round(X[t][i] 2^e) (int64, leading dimension
+// n).  The bound is taken in integers on the bits of the entries (an FP64
+// add runs at 1/64 of the FP32 rate here, and the sum of n FP64 adds per row
+// made this kernel FP64-bound): with emax the largest binary exponent of a
+// nonzero entry, each entry's significand is cut to at most 31 bits at
+// emax's scale and the cuts plus one per entry are summed in 64 bits, so
+// l1 <= U <= l1 (1 + n 2^-30) in those units: E is l1's own exponent unless
+// l1 lies within that factor below a power of two (then e is one smaller, a
+// quantisation step of 2^-60 instead of 2^-61 of l1).  Integer maxima and
+// sums do not depend on their order: e is reproducible run to run.
 constexpr int kQThreads = 256;
 
 // round(a 2^e) for |a 2^e| < 2^62, with integer operations on the bits of a
@@ -71,32 +80,89 @@ __device__ __forceinline__ long long quantize_bits(double a, int e) {
     return (bits >> 63) ? -(long long)q : (long long)q;
 }
 
+// rows are read in batches of kQBatch entries per thread, all loads first
+constexpr int kQBatch = 8;
+
 __global__ void __launch_bounds__(kQThreads)
 fx_quantize_kernel(const double *__restrict__ X, int64_t ldx, int64_t k, int64_t n,
                    long long *__restrict__ Q, int *__restrict__ expo) {
-    __shared__ double red[kQThreads / 32];
-    const int tid = threadIdx.x;
+    __shared__ int s_max[kQThreads / 32];
+    __shared__ unsigned long long s_sum[kQThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr unsigned long long kM52 = 0xFFFFFFFFFFFFFull;
+    constexpr int64_t kStep = (int64_t)kQBatch * kQThreads;
     for (int64_t t = blockIdx.x; t < k; t += gridDim.x) {
-        const double *row = X + t * ldx;
-        double s = 0.0;
-        for (int64_t i = tid; i < n; i += kQThreads) s += fabs(row[i]);
+        const unsigned long long *row = reinterpret_cast<const unsigned long long *>(X + t * ldx);
+        // the largest binary exponent field of a nonzero entry (1 for subnormals)
+        int mx = 0;
+        for (int64_t i0 = tid; i0 < n; i0 += kStep) {
+            unsigned long long b[kQBatch];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if ((tid & 31) == 0) red[tid >> 5] = s;
-        __syncthreads();
-        double l1 = 0.0;
+            for (int u = 0; u < kQBatch; ++u) {
+                const int64_t i = i0 + (int64_t)u * kQThreads;
+                b[u] = i < n ? row[i] : 0ull;
+            }
 #pragma unroll
-        for (int w = 0; w < kQThreads / 32; ++w) l1 += red[w];
+            for (int u = 0; u < kQBatch; ++u) {
+                const int ex = (int)((b[u] >> 52) & 0x7ff);
+                if (b[u] << 1) mx = max(mx, ex ? ex : 1);
+            }
+        }
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if (lane == 0) s_max[warp] = mx;
         __syncthreads();
+        int emax = 0;
+#pragma unroll
+        for (int w = 0; w < kQThreads / 32; ++w) emax = max(emax, s_max[w]);
         int e = 0;
-        if (l1 > 0.0) {
-            int E;
-            frexp(l1, &E);   // l1 < 2^E
+        if (emax > 0) {
+            // sum over the entries of floor(significand / 2^(emax - exponent + 22)) + 1
+            unsigned long long S = 0;
+            for (int64_t i0 = tid; i0 < n; i0 += kStep) {
+                unsigned long long b[kQBatch];
+#pragma unroll
+                for (int u = 0; u < kQBatch; ++u) {
+                    const int64_t i = i0 + (int64_t)u * kQThreads;
+                    b[u] = i < n ? row[i] : 0ull;
+                }
+#pragma unroll
+                for (int u = 0; u < kQBatch; ++u) {
+                    if (b[u] << 1) {
+                        const int ex = (int)((b[u] >> 52) & 0x7ff);
+                        const unsigned long long mant = (b[u] & kM52) | (ex ? 1ull << 52 : 0ull);
+                        const int sh = emax - (ex ? ex : 1) + 22;
+                        S += (sh < 64 ? mant >> sh : 0ull) + 1ull;
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
+            if (lane == 0) s_sum[warp] = S;
+            __syncthreads();
+            unsigned long long U = 0;
+#pragma unroll
+            for (int w = 0; w < kQThreads / 32; ++w) U += s_sum[w];
+            // l1 < U 2^(emax - 1075 + 22) <= 2^E
+            const int E = (64 - __clzll((long long)U)) + emax - 1053;
             e = 61 - E;
             e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
         }
+        __syncthreads();   // s_max and s_sum are reused by the next row
         long long *qrow = Q + t * n;
-        for (int64_t i = tid; i < n; i += kQThreads) qrow[i] = quantize_bits(row[i], e);
+        const double *xr = X + t * ldx;
+        for (int64_t i0 = tid; i0 < n; i0 += kStep) {
+            double a[kQBatch];
+#pragma unroll
+            for (int u = 0; u < kQBatch; ++u) {
+                const int64_t i = i0 + (int64_t)u * kQThreads;
+                a[u] = i < n ? xr[i] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < kQBatch; ++u) {
+                const int64_t i = i0 + (int64_t)u * kQThreads;
+                if (i < n) qrow[i] = quantize_bits(a[u], e);
+            }
+        }
         if (tid == 0) expo[t] = e;
     }
 }
