@@ -47,9 +47,10 @@ namespace {
 
 // ---------------------------------------------------------------- quantisation
 // One CTA per row t of X (k rows of n FP64 values, leading dimension ldx):
-// an upper bound U of l1 = sum |X[t][:]|, e[t] = 61 - E with U < 2^E, clamped
-// to [-1022, 1023], and Q[t][i] = round(X[t][i] 2^e) (int64, leading dimension
-// n).  The bound is taken in integers on the bits of the entries (an FP64
+// an upper bound U of l1 = sum |X[t][:]|, e[t] = 61 - E with U < 2^E, and
+// Q[t][i] = round(X[t][i] 2^e) (int64, leading dimension n; the scaling is a
+// shift of the significand, so e may leave the FP64 exponent range, as it does
+// for columns of norm below 2^-962).  The bound is taken in integers on the bits of the entries (an FP64
 // add runs at 1/64 of the FP32 rate here, and the sum of n FP64 adds per row
 // made this kernel FP64-bound): with emax the largest binary exponent of a
 // nonzero entry, each entry's significand is cut to at most 31 bits at
@@ -71,8 +72,8 @@ __device__ __forceinline__ long long quantize_bits(double a, int e) {
     if (ex) mant |= 1ull << 52;
     const int sh = (ex ? ex : 1) - 1075 + e;
     unsigned long long q;
-    if (sh >= 0)
-        q = sh < 11 ? mant << sh : 0ull;   // cannot happen for |a 2^e| < 2^62 beyond 9
+    if (sh >= 0)   // subnormal entries of a column of tiny norm: |a 2^e| < 2^62 bounds the shift
+        q = sh < 64 ? mant << sh : 0ull;
     else if (sh > -64)
         q = (mant + (1ull << (-sh - 1))) >> (-sh);
     else
@@ -144,8 +145,7 @@ fx_quantize_kernel(const double *__restrict__ X, int64_t ldx, int64_t k, int64_t
             for (int w = 0; w < kQThreads / 32; ++w) U += s_sum[w];
             // l1 < U 2^(emax - 1075 + 22) <= 2^E
             const int E = (64 - __clzll((long long)U)) + emax - 1053;
-            e = 61 - E;
-            e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
+            e = 61 - E;   // within [-995, 1112] for finite entries: 2^e need not be a double
         }
         __syncthreads();   // s_max and s_sum are reused by the next row
         long long *qrow = Q + t * n;

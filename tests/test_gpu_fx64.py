@@ -84,6 +84,51 @@ def test_fx64_extreme_column_scales(cmm):
     assert err <= TOL, err
 
 
+def _norm(x):
+    # 2-norm without overflow or underflow of the squares
+    s = np.abs(x).max()
+    return 0.0 if s == 0 else float(s * np.linalg.norm(x / s))
+
+
+def test_fx64_norms_at_powers_of_two_and_tiny_or_huge_columns(cmm):
+    # the per-column scale comes from an integer upper bound of the column's l1
+    # norm; each special column is checked alone (k = 1, so the tolerance is
+    # relative to that column's own norm product): a norm exactly a power of
+    # two, just below one (by 2^-40 and by one unit in the last place), just
+    # above one, entries near the bottom of the normal range (norm below
+    # 2^-962, where the scale 2^e leaves the FP64 range), one normal entry
+    # among subnormal ones, and entries near the top of the range
+    m, p, L, d = 640, 300, 14, 3
+    g = np.random.default_rng(11)
+    cols = {}
+    c = np.zeros(m)
+    c[:8] = 2.0 ** -3
+    cols["pow2"] = c                              # l1 = 1
+    c = np.full(m, 1.0 / 512.0)
+    c[0] -= 2.0 ** -40
+    cols["below_2^-40"] = c                       # l1 = 1.25 - 2^-40
+    c = np.zeros(m)
+    c[:2] = [0.5, np.nextafter(0.5, 0.0)]
+    cols["below_ulp"] = c                         # l1 one ulp below 1
+    c = np.zeros(m)
+    c[:2] = [0.5, np.nextafter(0.5, 1.0)]
+    cols["above_ulp"] = c                         # l1 one ulp above 1
+    cols["tiny"] = 1e-300 * g.standard_normal(m)
+    c = 1e-310 * g.integers(-3, 4, m).astype(np.float64)
+    c[17] = 1e-300
+    cols["normal_among_subnormal"] = c
+    cols["huge"] = 1e300 * g.standard_normal(m) / m
+    B = g.standard_normal((1, p))
+    h = cmm.make_hashes(2024, d, L)
+    for name, a in cols.items():
+        A = a.reshape(m, 1).copy()
+        R = cmm.sketch(_dev(A, torch.float64), _dev(B, torch.float64), h, prec="fx64").cpu().numpy()
+        Ro = orc.compress(A, B, h.params, L)
+        assert np.isfinite(R).all(), name
+        err = np.abs(R - Ro).max() / (_norm(a) * _norm(B[0]))
+        assert err <= TOL, (name, err)
+
+
 def test_fx64_deterministic_and_exact_on_small_integers(cmm):
     # bitwise-identical reruns; +-1 inputs within the tolerance (the
     # multiply-accumulate is float-float, so integer R is not guaranteed bit
