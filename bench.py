@@ -591,6 +591,7 @@ def run_cmm(a):
                          "ms_per_step": round(e2e_ms, 3), "steps": a.e2e_steps,
                          "call_ms_min": round(calls[0], 3),
                          "call_ms_median": round(calls[len(calls) // 2], 3),
+                         "call_ms_max": round(calls[-1], 3),
                          "api": "cmm_multiply_host (pinned host A, B, C, heavy-hitter list)",
                          "spans_ms_one_call": e2e_spans}
         del wsh
