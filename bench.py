@@ -573,6 +573,7 @@ def run_cmm(a):
                 calls.append((time.perf_counter() - c0) * 1e3)
             e2e_s = time.perf_counter() - t0
         e2e_ms = max_over_ranks(e2e_s * 1e3 / a.e2e_steps, world, dev)
+        slowest = int(np.argmax(calls))
         calls.sort()
         nhh = int(Ie.numel())
         # one more call, traced: device time of each copy and kernel span (the copies
@@ -591,7 +592,7 @@ def run_cmm(a):
                          "ms_per_step": round(e2e_ms, 3), "steps": a.e2e_steps,
                          "call_ms_min": round(calls[0], 3),
                          "call_ms_median": round(calls[len(calls) // 2], 3),
-                         "call_ms_max": round(calls[-1], 3),
+                         "call_ms_max": round(calls[-1], 3), "call_max_index": slowest,
                          "api": "cmm_multiply_host (pinned host A, B, C, heavy-hitter list)",
                          "spans_ms_one_call": e2e_spans}
         del wsh
