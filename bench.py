@@ -742,6 +742,39 @@ def run_batched(a):
                                               "f64": round(seq64 / best, 2)}
     out["R_err_vs_fp64_rel_to_sum_norms"] = err
     del Rb, R64, wsq
+    # the literal reading of the sketch-length rule (next power of two >= 8 x 16
+    # planted entries, at least 2^10): every problem at b = 2^10, default tiles,
+    # where reading A and B once from HBM is a bound of the same order as the
+    # butterflies
+    lit = [cmm.Problem(At, B, cmm.make_hashes(7000 + q, d, 10)) for q, (At, B, _, _) in enumerate(raw)]
+    lbatch = cmm.Batch(lit, d=d)
+    for _ in range(a.warmup):
+        lbatch.launch()
+    assert lbatch.status() == cmm.OK
+    lg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(lg):
+        lbatch.launch()
+    lclk = ClockSampler(0)
+    lclk.start()
+    lms = _events_ms(lg.replay, a.steps)
+    lclk = lclk.stop()
+    assert lbatch.status() == cmm.OK
+    lflops = sum(d * pb.At.shape[0] * (2.0 * 1024 * 10 + 1024) for pb in lit)
+    lbytes = float(sum((At.numel() + B.numel()) * 4 for (At, B, _, _) in raw))
+    hbm_gbs, hbm_kind, _ = peaks()
+    # Decompress of every entry: d gathers from R per entry, about one 8-byte
+    # gather per clock per SM (the extraction kernels' bound)
+    lgathers = float(sum(d * pb.At.shape[1] * pb.B.shape[1] for pb in lit))
+    out["literal_b1024"] = {
+        "ms": round(lms, 3), "clocks": lclk,
+        "extraction_gathers": lgathers,
+        "extraction_gather_bound_ms": round(lgathers / (152 * 2.07e9) * 1e3, 2),
+        "roofline": alu_roofline("batched_kernel", lflops, lms,
+                                 "per problem d*k*(2 b log2 b + b) at b = 2^10"),
+        "hbm_roofline": {"bytes_A_B": lbytes, "achieved_gbs": round(lbytes / (lms * 1e-3) / 1e9, 1),
+                         "peak_gbs": hbm_gbs, "peak_kind": hbm_kind,
+                         "frac": round(lbytes / (lms * 1e-3) / 1e9 / hbm_gbs, 4)}}
+    del lit, lbatch, lg
     if not a.no_cpu:
         out["cpu_baseline"] = batched_oracle(raw, probs, d, nsample=32)
     res = {"metric": "batched: 256 uneven problems (sketch + FP64 finish + median extraction), "

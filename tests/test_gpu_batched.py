@@ -170,3 +170,25 @@ def test_batched_256_uneven_problems(cmm):
     rows = (5, 9)
     Co = orc.extract(R, pb.hashes.params, A.shape[0], B.shape[1], rows=rows)
     assert np.array_equal(pb.C[rows[0]:rows[1]].cpu().numpy(), Co)
+
+
+def test_batched_256_problems_literal_b1024(cmm):
+    # the literal sketch-length rule (every problem at b = 2^10) on the same 256
+    # operand pairs: the smallest and the largest problem in full against the
+    # oracle (whole R, whole estimate given the same R)
+    d = 5
+    raw = wl.batch_problems_device(count=256, seed=1004, device="cuda")
+    probs = [cmm.Problem(At, B, cmm.make_hashes(7000 + q, d, 10)) for q, (At, B, _, _) in enumerate(raw)]
+    batch = cmm.Batch(probs, d=d)
+    batch.launch()
+    assert batch.status() == cmm.OK
+    size = [pb.At.shape[0] * pb.At.shape[1] * pb.B.shape[1] for pb in probs]
+    for q in (int(np.argmin(size)), int(np.argmax(size))):
+        pb = probs[q]
+        A = pb.At.double().cpu().numpy().T.copy()
+        B = pb.B.double().cpu().numpy()
+        Ro = orc.compress(A, B, pb.hashes.params, 10, nthreads=orc.max_threads())
+        R = pb.R.cpu().numpy()
+        assert np.abs(R - Ro).max() <= 1e-5 * _scale(A, B), q
+        Co = orc.extract(R, pb.hashes.params, A.shape[0], B.shape[1], nthreads=8)
+        assert np.array_equal(pb.C.cpu().numpy(), Co), q
