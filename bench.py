@@ -564,6 +564,8 @@ def run_cmm(a):
         torch.cuda.synchronize()
         barrier()
         calls = []
+        eclk = ClockSampler(local)
+        eclk.start()
         with no_gc():
             t0 = time.perf_counter()
             for _ in range(a.e2e_steps):
@@ -572,6 +574,7 @@ def run_cmm(a):
                                                     capacity=cap, hh_out=hh, ws=wsh)
                 calls.append((time.perf_counter() - c0) * 1e3)
             e2e_s = time.perf_counter() - t0
+        eclk = eclk.stop()
         e2e_ms = max_over_ranks(e2e_s * 1e3 / a.e2e_steps, world, dev)
         slowest = int(np.argmax(calls))
         calls.sort()
@@ -593,6 +596,7 @@ def run_cmm(a):
                          "call_ms_min": round(calls[0], 3),
                          "call_ms_median": round(calls[len(calls) // 2], 3),
                          "call_ms_max": round(calls[-1], 3), "call_max_index": slowest,
+                         "clocks": eclk,
                          "api": "cmm_multiply_host (pinned host A, B, C, heavy-hitter list)",
                          "spans_ms_one_call": e2e_spans}
         del wsh
