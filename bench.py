@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--no-dgemm", action="store_true", help="skip the cuBLAS DGEMM comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=60)
     ap.add_argument("--workload", default="planted",
                     choices=["planted", "batched", "precision", "diff", "cyclic", "paper",
                              "instances"],
@@ -221,7 +221,10 @@ class ClockSampler:
         self.proc = None
         self.path = None
 
-    def start(self):
+    def start(self, ready_s: float = 5.0):
+        """Start sampling and return once the first sample is written (at most
+        `ready_s` seconds): nvidia-smi's start-up queries the driver, and a
+        timed region that overlaps it can see one call stalled by tens of ms."""
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
@@ -231,6 +234,13 @@ class ClockSampler:
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t_end = time.perf_counter() + ready_s
+        while time.perf_counter() < t_end and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
+        time.sleep(0.25)   # past the second sample as well
 
     def stop(self):
         if self.proc is None:
@@ -577,6 +587,9 @@ def run_cmm(a):
         eclk = eclk.stop()
         e2e_ms = max_over_ranks(e2e_s * 1e3 / a.e2e_steps, world, dev)
         slowest = int(np.argmax(calls))
+        # calls more than 2 ms above the median (host-side stalls: the device-timed
+        # steps of the same work show none)
+        slow_calls = int(sum(c > float(np.median(calls)) + 2.0 for c in calls))
         calls.sort()
         nhh = int(Ie.numel())
         # one more call, traced: device time of each copy and kernel span (the copies
@@ -596,6 +609,7 @@ def run_cmm(a):
                          "call_ms_min": round(calls[0], 3),
                          "call_ms_median": round(calls[len(calls) // 2], 3),
                          "call_ms_max": round(calls[-1], 3), "call_max_index": slowest,
+                         "calls_over_median_plus_2ms": slow_calls,
                          "clocks": eclk,
                          "api": "cmm_multiply_host (pinned host A, B, C, heavy-hitter list)",
                          "spans_ms_one_call": e2e_spans}

@@ -53,9 +53,10 @@ __device__ __forceinline__ void gather_keys(const T *Sg, T *acc, int64_t n, uint
                                             uint64_t as, uint64_t cs, int shift, uint32_t u_hi,
                                             int q) {
     using S = FwhtShape<T, L, LE>;
-    for (int64_t x = q; x < n; x += S::P) {
-        const uint32_t h = mas_hash(a, c, (uint64_t)x, shift);
-        const uint32_t neg = mas_sign_bit(as, cs, (uint64_t)x) ^ (__popc((h >> L) & u_hi) & 1u);
+    MasWalk hw(a, c, (uint64_t)q, S::P), sw(as, cs, (uint64_t)q, S::P);
+    for (int64_t x = q; x < n; x += S::P, hw.next(), sw.next()) {
+        const uint32_t h = hw.top(shift);
+        const uint32_t neg = sw.top(63) ^ (__popc((h >> L) & u_hi) & 1u);
         const T v = Sg[pad_index<T, L, LE>((int)(h & (S::N - 1)))];
         acc[x] += neg ? -v : v;
     }

@@ -301,4 +301,14 @@ __device__ __forceinline__ uint32_t mas_sign_bit(uint64_t a, uint64_t c, uint64_
     return (uint32_t)((a * x + c) >> 63);   // 1 means the sign -1
 }
 
+// (a x + c) mod 2^64 along x0, x0 + D, x0 + 2 D, ...: one 64-bit add per step
+// instead of a multiply (the same values as mas_hash and mas_sign_bit)
+struct MasWalk {
+    uint64_t v, step;
+    __device__ __forceinline__ MasWalk(uint64_t a, uint64_t c, uint64_t x0, uint64_t d)
+        : v(a * x0 + c), step(a * d) {}
+    __device__ __forceinline__ uint32_t top(int shift) const { return (uint32_t)(v >> shift); }
+    __device__ __forceinline__ void next() { v += step; }
+};
+
 }  // namespace cmm

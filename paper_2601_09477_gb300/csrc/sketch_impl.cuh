@@ -59,6 +59,7 @@ __device__ __forceinline__ void scatter_column(T *Sg, const T *__restrict__ col,
     using S = FwhtShape<T, L, LE>;
     constexpr int P = S::P;
     constexpr int B = 8;
+    MasWalk hw(a, c, (uint64_t)q, P), sw(as, cs, (uint64_t)q, P);   // at x = i + e P
     int64_t i = q;
     for (; i + (B - 1) * (int64_t)P < n; i += B * (int64_t)P) {
         T val[B];
@@ -66,9 +67,10 @@ __device__ __forceinline__ void scatter_column(T *Sg, const T *__restrict__ col,
         for (int e = 0; e < B; ++e) val[e] = ld_stream(col + i + e * (int64_t)P);
 #pragma unroll
         for (int e = 0; e < B; ++e) {
-            const uint64_t x = (uint64_t)(i + e * (int64_t)P);
-            const uint32_t h = mas_hash(a, c, x, shift);
-            const uint32_t neg = mas_sign_bit(as, cs, x) ^ (__popc((h >> L) & u_hi) & 1u);
+            const uint32_t h = hw.top(shift);
+            const uint32_t neg = sw.top(63) ^ (__popc((h >> L) & u_hi) & 1u);
+            hw.next();
+            sw.next();
             atomicAdd(Sg + pad_index<T, L, LE>((int)(h & (S::N - 1))), neg_if(val[e], neg));
         }
     }
@@ -79,12 +81,12 @@ __device__ __forceinline__ void scatter_column(T *Sg, const T *__restrict__ col,
             val[e] = i + e * (int64_t)P < n ? ld_stream(col + i + e * (int64_t)P) : T(0);
 #pragma unroll
         for (int e = 0; e < B; ++e) {
-            if (i + e * (int64_t)P < n) {
-                const uint64_t x = (uint64_t)(i + e * (int64_t)P);
-                const uint32_t h = mas_hash(a, c, x, shift);
-                const uint32_t neg = mas_sign_bit(as, cs, x) ^ (__popc((h >> L) & u_hi) & 1u);
+            const uint32_t h = hw.top(shift);
+            const uint32_t neg = sw.top(63) ^ (__popc((h >> L) & u_hi) & 1u);
+            hw.next();
+            sw.next();
+            if (i + e * (int64_t)P < n)
                 atomicAdd(Sg + pad_index<T, L, LE>((int)(h & (S::N - 1))), neg_if(val[e], neg));
-            }
         }
     }
 }
@@ -145,10 +147,10 @@ __device__ __forceinline__ int block_cmax(int *S0, const tab_t *__restrict__ tab
                                           uint64_t a, uint64_t c, int shift, int *red) {
     using S = FwhtShape<float, L, LE>;
     static_assert(THREADS % 32 == 0 && THREADS <= 1024, "whole warps");
-    for (int64_t i = threadIdx.x; i < n; i += THREADS) {
+    MasWalk hw(a, c, threadIdx.x, THREADS);
+    for (int64_t i = threadIdx.x; i < n; i += THREADS, hw.next()) {
         const int w = tab ? (int)(__ldg(tab + i) & 0x7fffu)
-                          : pad_index<float, L, LE>((int)(mas_hash(a, c, (uint64_t)i, shift) &
-                                                          (uint32_t)(S::N - 1)));
+                          : pad_index<float, L, LE>((int)(hw.top(shift) & (uint32_t)(S::N - 1)));
         atomicAdd(S0 + w, 1);
     }
     __syncthreads();
@@ -176,6 +178,7 @@ __device__ __forceinline__ void scatter_column_fixed(int *Sg, const float *__res
     using S = FwhtShape<float, L, LE>;
     constexpr int P = S::P;
     constexpr int B = 8;
+    MasWalk hw(a, c, (uint64_t)q, P), sw(as, cs, (uint64_t)q, P);   // at x = i + e P
     int64_t i = q;
     for (; i + (B - 1) * (int64_t)P < n; i += B * (int64_t)P) {
         float val[B];
@@ -183,9 +186,10 @@ __device__ __forceinline__ void scatter_column_fixed(int *Sg, const float *__res
         for (int e = 0; e < B; ++e) val[e] = ld_stream(col + i + e * (int64_t)P);
 #pragma unroll
         for (int e = 0; e < B; ++e) {
-            const uint64_t x = (uint64_t)(i + e * (int64_t)P);
-            const uint32_t h = mas_hash(a, c, x, shift);
-            const uint32_t neg = mas_sign_bit(as, cs, x) ^ (__popc((h >> L) & u_hi) & 1u);
+            const uint32_t h = hw.top(shift);
+            const uint32_t neg = sw.top(63) ^ (__popc((h >> L) & u_hi) & 1u);
+            hw.next();
+            sw.next();
             const int iv = __float2int_rn(val[e] * s);
             atomicAdd(Sg + pad_index<float, L, LE>((int)(h & (S::N - 1))), neg ? -iv : iv);
         }
@@ -197,13 +201,13 @@ __device__ __forceinline__ void scatter_column_fixed(int *Sg, const float *__res
             val[e] = i + e * (int64_t)P < n ? ld_stream(col + i + e * (int64_t)P) : 0.f;
 #pragma unroll
         for (int e = 0; e < B; ++e) {
-            if (i + e * (int64_t)P < n) {
-                const uint64_t x = (uint64_t)(i + e * (int64_t)P);
-                const uint32_t h = mas_hash(a, c, x, shift);
-                const uint32_t neg = mas_sign_bit(as, cs, x) ^ (__popc((h >> L) & u_hi) & 1u);
-                const int iv = __float2int_rn(val[e] * s);
+            const uint32_t h = hw.top(shift);
+            const uint32_t neg = sw.top(63) ^ (__popc((h >> L) & u_hi) & 1u);
+            hw.next();
+            sw.next();
+            const int iv = __float2int_rn(val[e] * s);
+            if (i + e * (int64_t)P < n)
                 atomicAdd(Sg + pad_index<float, L, LE>((int)(h & (S::N - 1))), neg ? -iv : iv);
-            }
         }
     }
 }
