@@ -780,13 +780,26 @@ def run_batched(a):
     lflops = sum(d * pb.At.shape[0] * (2.0 * 1024 * 10 + 1024) for pb in lit)
     lbytes = float(sum((At.numel() + B.numel()) * 4 for (At, B, _, _) in raw))
     hbm_gbs, hbm_kind, _ = peaks()
-    # Decompress of every entry: d gathers from R per entry, about one 8-byte
-    # gather per clock per SM (the extraction kernels' bound)
+    # the same launch without the extraction tasks (the problems' R reused, no
+    # C): the sketch and finish alone, and Decompress by difference; at b = 2^10
+    # each extraction task stages R in shared memory, so its d gathers per entry
+    # are shared-memory loads
+    skp = [cmm.Problem(pb.At, pb.B, pb.hashes, R=pb.R) for pb in lit]
+    sbatch = cmm.Batch(skp, d=d, with_C=False)
+    for _ in range(a.warmup):
+        sbatch.launch()
+    assert sbatch.status() == cmm.OK
+    sms = _events_ms(sbatch.launch, a.steps)
+    assert sbatch.status() == cmm.OK
+    del skp, sbatch
     lgathers = float(sum(d * pb.At.shape[1] * pb.B.shape[1] for pb in lit))
+    ext_ms = max(lms - sms, 1e-6)
     out["literal_b1024"] = {
         "ms": round(lms, 3), "clocks": lclk,
+        "sketch_and_finish_ms": round(sms, 3),
+        "extraction_ms_by_difference": round(lms - sms, 3),
         "extraction_gathers": lgathers,
-        "extraction_gather_bound_ms": round(lgathers / (152 * 2.07e9) * 1e3, 2),
+        "extraction_gathers_per_clock_per_sm": round(lgathers / (ext_ms * 1e-3) / (152 * 2.07e9), 2),
         "roofline": alu_roofline("batched_kernel", lflops, lms,
                                  "per problem d*k*(2 b log2 b + b) at b = 2^10"),
         "hbm_roofline": {"bytes_A_B": lbytes, "achieved_gbs": round(lbytes / (lms * 1e-3) / 1e9, 1),
