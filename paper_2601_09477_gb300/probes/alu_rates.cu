@@ -1,6 +1,7 @@
 // alu_rates.cu -- throughput of the arithmetic the sketch kernels are built
 // from, measured on the device it runs on: FP32 add (scalar and packed
-// FP32x2), FP64 add, 32- and 64-bit integer add, 32-bit integer multiply-add,
+// FP32x2), FP64 add, 32- and 64-bit integer add, 64-bit integer radix-4
+// butterflies, 32-bit integer multiply-add,
 // 64-bit -> FP32 and 32-bit -> FP32 conversions, and 32- / 64-bit integer
 // atomic adds to distinct shared-memory words.  Each kernel runs a fixed
 // number of independent operation chains per thread (no memory traffic in
@@ -217,6 +218,40 @@ __global__ void k_atoms64(float *sink, unsigned long long y) {
     note_clock(c0);
 }
 
+// Walsh-Hadamard butterflies on 64-bit integers in the form the fixed-point
+// sketch runs them: 16 values per thread, four stages as two radix-4 passes
+// (each output one three-input add or subtract), counted as one operation per
+// value per stage.  A constant added to one value per transform keeps the
+// values from settling; 64 registers at most, so that 4 CTAs stay resident.
+__global__ void __launch_bounds__(kThreads, 4) k_r4_s64(float *sink, long long y) {
+    const long long c0 = clock64();
+    long long v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = threadIdx.x * 16 + j;
+    for (int it = 0; it < kIters / 8; ++it) {
+#pragma unroll
+        for (int h = 1; h < 16; h *= 4) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                if ((j & (3 * h)) == 0) {
+                    const long long a = v[j], b = v[j + h], c = v[j + 2 * h], d = v[j + 3 * h];
+                    const long long s1 = a + b, d1 = a - b;
+                    v[j] = s1 + c + d;
+                    v[j + h] = d1 + c - d;
+                    v[j + 2 * h] = s1 - c - d;
+                    v[j + 3 * h] = d1 - c + d;
+                }
+            }
+        }
+        v[0] += y;
+    }
+    long long s = 0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) s ^= v[j];
+    sink[blockIdx.x * blockDim.x + threadIdx.x] = (float)s;
+    note_clock(c0);
+}
+
 template <typename K, typename Y>
 int run(const char *name, K kern, Y y, double ops_per_thread, int sms, float *sink, int blocks,
         bool first) {
@@ -271,6 +306,7 @@ int main() {
     rc |= run("dadd_f64", k_dadd, 1.0, n / 16, sms, sink, blocks, false);
     rc |= run("add_s32", k_iadd32, 3, n, sms, sink, blocks, false);
     rc |= run("add_s64", k_iadd64, 3ll, n, sms, sink, blocks, false);
+    rc |= run("fwht_r4_s64", k_r4_s64, 3ll, (double)(kIters / 8) * 4 * 16, sms, sink, blocks, false);
     rc |= run("mad_lo_s32", k_imad32, 3, n, sms, sink, blocks, false);
     rc |= run("cvt_f32_s64", k_cvt_s64_f32, 3ll, n / 4, sms, sink, blocks, false);
     rc |= run("cvt_f32_s32", k_cvt_s32_f32, 3, n / 4, sms, sink, blocks, false);
